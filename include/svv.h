@@ -1,0 +1,171 @@
+/*
+ * svv.h -- C ABI of libsvv: stable-vertex-value queries over the snapshots of an
+ * evolving graph, on one GB300 GPU (sm_103a).
+ *
+ * The method (arXiv 2502.10579):
+ *   Section 3, Step 1 / Algorithm 1: solve the query on the intersection graph
+ *     (edges present in every snapshot of the window) and on the union graph
+ *     (present in any), giving per-vertex bounds (Theorem 1, Table 1).
+ *   Section 3, Step 2 / Theorem 2: a vertex whose two bounds agree is stable:
+ *     its value is the same in every snapshot.
+ *   Section 3, Step 3-4: drop the in-edges of stable vertices (the Q-relevant
+ *     subgraph) and the additions whose sink is stable.
+ *   Section 4 / Algorithm 2: relax every snapshot of the window concurrently
+ *     over that subgraph, from the intersection-graph values, with one
+ *     snapshot-oblivious frontier and a per-edge snapshot-presence bitmask
+ *     (Section 4.1, versioned graph).
+ * The result equals, bit for bit, a from-scratch solve of every snapshot.
+ *
+ * Conventions used by every call:
+ *   - Vertices are 0..V-1 and exist in every snapshot (Section 2).  The graph is
+ *     a multigraph of edge INSTANCES: a re-added edge is a new instance with its
+ *     own weight and mask, which gives the minimum-weight reading of Section 3
+ *     (maximum for SSWP) without merging.
+ *   - Presence masks: W = ceil(S/64) uint64 words per edge, edge-major
+ *     (mask[e*W + k]); bit b of word k says the edge is present in snapshot
+ *     64k+b, so the least significant bit of word 0 is snapshot 0 (Section 4.1,
+ *     version labels).  Bits >= S are ignored.
+ *   - Values are uint32.  SSSP: distance, source 0, unreachable 0xFFFFFFFF,
+ *     sums saturate at 0xFFFFFFFE.  BFS: hop count, source 0, unreachable
+ *     0xFFFFFFFF.  SSWP: width, source 0xFFFFFFFF (+inf), unreachable 0.
+ *     (Table 2 edge functions; the paper leaves the encodings unstated.)
+ *   - Output layout: out[i*V + v] is the value of v in snapshot win_begin+i,
+ *     for 0 <= i < win_len (snapshot-major, win_len x V).
+ *   - Nothing throws or aborts across this ABI; every call returns a status.
+ *     Every device spin-wait is bounded; an expired wait or the iteration cap
+ *     returns SVV_ETIMEOUT and the context stays usable.
+ *   - A context is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef SVV_H
+#define SVV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct svv_ctx svv_ctx; /* opaque, owned by the library */
+
+typedef enum { SVV_SSSP = 0, SVV_SSWP = 1, SVV_BFS = 2 } svv_type;
+
+typedef enum {
+    SVV_OK = 0,
+    SVV_EINVAL = 1,      /* bad argument (message via svv_last_error) */
+    SVV_ENOMEM = 2,      /* device allocation failed or over the HBM budget */
+    SVV_ECUDA = 3,       /* a CUDA call failed */
+    SVV_ETIMEOUT = 4,    /* a bounded device wait expired or the iteration cap was hit */
+    SVV_EBUSY = 5,       /* serving queue full */
+    SVV_ENOTLOADED = 6,  /* no graph loaded */
+    SVV_EINTERNAL = 7    /* internal capacity check failed (a library bug) */
+} svv_status;
+
+/* Per-query diagnostics of the last svv_query / svv_query_plain call. */
+typedef struct {
+    uint32_t unstable;        /* U: vertices whose bounds differ (Section 3, Step 2) */
+    uint32_t qrs_edges;       /* edges of the Q-relevant subgraph kept for relaxation */
+    uint32_t qrs_masked;      /* of those, edges not present in every window snapshot */
+    uint32_t iters_cap;       /* frontier rounds of the intersection-graph solve */
+    uint32_t iters_cup;       /* frontier rounds of the union-graph solve */
+    uint32_t iters_relax;     /* frontier rounds of the multi-snapshot relaxation */
+    uint32_t iters_plain_max; /* largest round count of a per-snapshot solve */
+    uint32_t phase_timing;    /* 1 if the ms_* fields below were measured */
+    uint64_t edges_relaxed_cap, edges_relaxed_cup, edges_relaxed_multi;
+    /* device time of each phase (CUDA events on the query stream), when the
+     * "phase_timing" tuning key is 1: intersection solve, union solve, stable
+     * compaction + subgraph extraction, multi-snapshot relaxation, scatter;
+     * for svv_query_plain, ms_cap holds the total of the per-snapshot solves */
+    float ms_cap, ms_cup, ms_qrs, ms_relax, ms_scatter;
+    float reserved;
+} svv_stats;
+
+/* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the bytes
+ * the library allocates on the device (resident graph plus query scratch);
+ * 0 means "free memory at load time".  No device memory is allocated here. */
+svv_status svv_create(svv_ctx **ctx, int device, uint64_t hbm_budget_bytes);
+
+/* Host-side builder of the versioned union graph (Section 4.1): one edge per
+ * instance k with t_add[k] < t_del[k], grouped by source in instance order,
+ * mask bit i set iff t_add[k] <= i < t_del[k] (instance live in snapshot i).
+ * Inputs are host arrays of n_inst entries; outputs are caller-owned host
+ * arrays: row_ptr[V+1], col[n_inst], weight[n_inst], mask[n_inst*ceil(S/64)].
+ * *E_out receives the number of edges written.  SVV_EINVAL on src/dst >= V,
+ * S == 0 or t_add/t_del > S. */
+svv_status svv_build_versioned_csr(uint32_t V, uint32_t S, uint64_t n_inst, const uint32_t *src,
+                                   const uint32_t *dst, const uint32_t *w, const uint32_t *t_add,
+                                   const uint32_t *t_del, uint64_t *row_ptr, uint32_t *col,
+                                   uint32_t *weight, uint64_t *mask, uint64_t *E_out);
+
+/* Load the union CSR with per-edge presence masks (Section 4.1) and keep it
+ * resident on the device.  Arrays: row_ptr[V+1] (row_ptr[0]=0, non-decreasing,
+ * row_ptr[V]=E), col[E] (< V), weight[E], mask[E*ceil(S/64)] edge-major.  They
+ * live on the host, or on the device when inputs_on_device != 0; the library
+ * copies them and the caller keeps ownership.  Internally each row is reordered
+ * so that edges present in all S snapshots come first (Section 4.1), and edges
+ * present in no snapshot are dropped.  Replaces any graph loaded before.
+ * SVV_EINVAL on a malformed CSR, S == 0, V >= 2^32-1 or E >= 2^32;
+ * SVV_ENOMEM if the resident graph does not fit the budget. */
+svv_status svv_load(svv_ctx *ctx, uint32_t V, uint64_t E, uint32_t S, const uint64_t *row_ptr,
+                    const uint32_t *col, const uint32_t *weight, const uint64_t *mask,
+                    int inputs_on_device);
+
+/* One query through the intersection-union path (Algorithms 1 and 2):
+ * bounds on the window's intersection and union graphs, stable-vertex
+ * compaction, Q-relevant subgraph extraction, concurrent relaxation of all
+ * window snapshots, and the scatter into `out`.  `out` is a caller-owned
+ * DEVICE buffer of win_len*V uint32 (e.g. a torch tensor).  Work is ordered on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream); the call
+ * returns after the stream reaches the end of the query, with its status.
+ * `out` is written only when the result is SVV_OK.
+ * SVV_EINVAL on type, source >= V, win_len == 0 or win_begin+win_len > S. */
+svv_status svv_query(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
+                     uint32_t win_len, uint32_t *out, void *cuda_stream);
+
+/* The same query answered the plain way (Fig. 2a): one full solve per window
+ * snapshot, each written straight into its row of `out`.  Same arguments and
+ * output as svv_query; on failure the rows of `out` are unspecified. */
+svv_status svv_query_plain(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
+                           uint32_t win_len, uint32_t *out, void *cuda_stream);
+
+/* svv_query with `out_host` a HOST buffer of win_len*V uint32 (pinned memory
+ * is fastest): the device result is copied back inside the call. */
+svv_status svv_query_host(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
+                          uint32_t win_len, uint32_t *out_host, void *cuda_stream);
+
+/* Step-level results of the last successful svv_query, for inspection: the
+ * intersection-graph values (Section 3 Step 1, upper bound for SSSP/BFS, lower
+ * for SSWP), the union-graph values, and the vertex -> relaxation-row map
+ * (0xFFFFFFFF for a stable vertex, Theorem 2).  Each destination is a caller
+ * DEVICE buffer of V uint32 and may be NULL.  The copies are ordered on
+ * `cuda_stream` and complete before the call returns. */
+svv_status svv_get_bounds(svv_ctx *ctx, uint32_t *cap, uint32_t *cup, uint32_t *row,
+                          void *cuda_stream);
+
+/* Tuning knobs, by name: "max_iters" (frontier-round cap per solve, 0 = V+2),
+ * "spin_limit_ms" (bound on every device-side wait, default 1000),
+ * "solve_chunk" / "relax_chunk" / "qrs_chunk" (edges per work unit, powers of
+ * two), "blocks_per_sm" (0 = occupancy limit), "phase_timing" (1 = record
+ * CUDA events between the phases of each query, reported by svv_get_stats).  SVV_EINVAL on an unknown key
+ * or a value out of range. */
+svv_status svv_set_tuning(svv_ctx *ctx, const char *key, int64_t value);
+
+/* Diagnostics of the last completed query. */
+svv_status svv_get_stats(svv_ctx *ctx, svv_stats *out);
+
+/* Bytes currently allocated on the device by this context. */
+uint64_t svv_device_bytes(const svv_ctx *ctx);
+
+/* Human-readable name of a status. */
+const char *svv_status_str(svv_status s);
+
+/* Detail of the last error on this context ("" if none). */
+const char *svv_last_error(const svv_ctx *ctx);
+
+/* Free every device allocation and the context.  NULL is ignored. */
+void svv_destroy(svv_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVV_H */

@@ -1,0 +1,751 @@
+// svv_api.cu -- the C ABI declared in include/svv.h: context, resident graph,
+// scratch sizing and the stream-ordered query pipelines.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/svv.h"
+#include "svv_internal.h"
+
+using namespace svv;
+
+namespace {
+
+constexpr int kNumCtl = 8 + 256;  // 0..3 query phases, 8.. per-snapshot plain solves
+constexpr uint32_t kMaxSlab = 128;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct svv_ctx {
+  int device = 0;
+  uint64_t budget = 0;      // 0 until a graph is loaded if the caller passed 0
+  bool budget_auto = false;
+  uint64_t allocated = 0;
+  int num_sms = 0;
+  std::string err;
+
+  // tuning
+  uint32_t maxit = 0;
+  uint32_t spin_ms = 1000;
+  uint32_t solve_cs = 6, relax_cs = 5, qrs_cs = 8;
+  int bps = 0;
+  int threads = 512;
+  int occ_solve = 0, occ_qrs = 0, occ_relax = 0;
+  bool phase_timing = false;
+  cudaEvent_t ev[7] = {};
+
+  // resident graph
+  bool loaded = false;
+  DevGraph g{};
+  std::vector<void*> graph_bufs;
+
+  // query scratch (sized at load from V and E; the L-dependent part on demand)
+  std::vector<void*> scratch_bufs;
+  uint32_t *rI = nullptr, *rU = nullptr, *stamp = nullptr, *row = nullptr, *uv = nullptr;
+  uint32_t *part = nullptr, *qcnt = nullptr, *cur = nullptr, *qerr = nullptr;
+  uint4* qrow = nullptr;
+  uint2* qcw = nullptr;
+  unsigned long long *q0 = nullptr, *q1 = nullptr, *units = nullptr;
+  uint32_t qcap = 0, ucap = 0, ecap = 0;
+  TeamCtl* ctl = nullptr;
+  TeamCtl* hctl = nullptr;  // pinned mirror
+  uint32_t* hqerr = nullptr;
+  // window-dependent
+  uint64_t* qmask = nullptr;
+  uint64_t mcap = 0;
+  uint32_t* val = nullptr;
+  uint64_t valcap = 0;
+  uint32_t* staging = nullptr;  // device output for svv_query_host
+  uint64_t staging_cap = 0;
+
+  svv_stats stats{};
+};
+
+namespace {
+
+svv_status fail(svv_ctx* c, svv_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+svv_status cuda_fail(svv_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // clear a sticky launch error where possible
+  return fail(c, e == cudaErrorMemoryAllocation ? SVV_ENOMEM : SVV_ECUDA, m);
+}
+
+svv_status dev_alloc(svv_ctx* c, std::vector<void*>& owner, size_t bytes, void** out) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (c->budget && c->allocated + bytes > c->budget)
+    return fail(c, SVV_ENOMEM,
+                "device budget exceeded: need " + std::to_string(c->allocated + bytes) + " of " +
+                    std::to_string(c->budget) + " bytes");
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    cudaGetLastError();
+    return fail(c, SVV_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  owner.push_back(*out);
+  c->allocated += bytes;
+  return SVV_OK;
+}
+
+template <class T>
+svv_status alloc_n(svv_ctx* c, std::vector<void*>& owner, uint64_t n, T** out) {
+  return dev_alloc(c, owner, (size_t)n * sizeof(T), reinterpret_cast<void**>(out));
+}
+
+void free_list(svv_ctx* c, std::vector<void*>& bufs) {
+  for (void* p : bufs) cudaFree(p);
+  bufs.clear();
+}
+
+void free_graph(svv_ctx* c) {
+  free_list(c, c->graph_bufs);
+  free_list(c, c->scratch_bufs);
+  c->allocated = 0;
+  c->loaded = false;
+  c->g = DevGraph{};
+  c->qmask = nullptr;
+  c->val = nullptr;
+  c->staging = nullptr;
+  c->mcap = c->valcap = c->staging_cap = 0;
+}
+
+uint32_t ceil_div(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+LaunchCfg cfg_for(const svv_ctx* c, int occ) {
+  int per_sm = occ;
+  if (c->bps > 0) per_sm = std::min(per_sm, c->bps);
+  per_sm = std::max(1, std::min(per_sm, 4));
+  return LaunchCfg{c->num_sms * per_sm, c->threads};
+}
+
+// slab shape for the relaxation: P lanes per edge, K snapshots per lane
+void slab_shape(uint32_t ls, uint32_t& P, uint32_t& K) {
+  if (ls <= 8) {
+    P = 8;
+    K = 1;
+  } else if (ls <= 16) {
+    P = 16;
+    K = 1;
+  } else if (ls <= 32) {
+    P = 32;
+    K = 1;
+  } else if (ls <= 64) {
+    P = 32;
+    K = 2;
+  } else {
+    P = 32;
+    K = 4;
+  }
+}
+
+svv_status ensure_window(svv_ctx* c, uint32_t L) {
+  const uint32_t QW = ceil_div(L, 64);
+  const uint64_t need_m = (uint64_t)std::max<uint32_t>(c->g.NF, 1) * QW;
+  uint32_t P, K;
+  slab_shape(std::min(L, kMaxSlab), P, K);
+  const uint64_t need_v = (uint64_t)std::max<uint32_t>(c->g.V, 1) * P * K;
+  if (need_m > c->mcap) {
+    if (c->qmask) {
+      auto it = std::find(c->scratch_bufs.begin(), c->scratch_bufs.end(), (void*)c->qmask);
+      if (it != c->scratch_bufs.end()) c->scratch_bufs.erase(it);
+      cudaFree(c->qmask);
+      c->allocated -= ((c->mcap * 8 + 255) & ~uint64_t(255));
+      c->qmask = nullptr;
+      c->mcap = 0;
+    }
+    svv_status s = alloc_n(c, c->scratch_bufs, need_m, &c->qmask);
+    if (s) return s;
+    c->mcap = need_m;
+  }
+  if (need_v > c->valcap) {
+    if (c->val) {
+      auto it = std::find(c->scratch_bufs.begin(), c->scratch_bufs.end(), (void*)c->val);
+      if (it != c->scratch_bufs.end()) c->scratch_bufs.erase(it);
+      cudaFree(c->val);
+      c->allocated -= ((c->valcap * 4 + 255) & ~uint64_t(255));
+      c->val = nullptr;
+      c->valcap = 0;
+    }
+    svv_status s = alloc_n(c, c->scratch_bufs, need_v, &c->val);
+    if (s) return s;
+    c->valcap = need_v;
+  }
+  return SVV_OK;
+}
+
+svv_status check_query(svv_ctx* c, int type, uint32_t source, uint32_t wb, uint32_t wl, const void* out) {
+  if (!c) return SVV_EINVAL;
+  if (!c->loaded) return fail(c, SVV_ENOTLOADED, "no graph loaded");
+  if (type < 0 || type > 2) return fail(c, SVV_EINVAL, "unknown query type");
+  if (source >= c->g.V) return fail(c, SVV_EINVAL, "source >= V");
+  if (wl == 0) return fail(c, SVV_EINVAL, "win_len == 0");
+  if ((uint64_t)wb + wl > c->g.S) return fail(c, SVV_EINVAL, "win_begin + win_len > S");
+  if (!out) return fail(c, SVV_EINVAL, "out is NULL");
+  return SVV_OK;
+}
+
+SolveArgs solve_base(svv_ctx* c, uint32_t wb, uint32_t wl) {
+  SolveArgs a{};
+  a.g = c->g;
+  a.win = Window{wb, wl};
+  a.stamp = c->stamp;
+  a.q0 = c->q0;
+  a.q1 = c->q1;
+  a.qcap = c->qcap;
+  a.cshift = c->solve_cs;
+  a.qerr = c->qerr;
+  a.maxit = c->maxit ? c->maxit : c->g.V + 2u;
+  a.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
+  return a;
+}
+
+svv_status finish(svv_ctx* c, cudaStream_t s, int nctl_copy) {
+  cudaError_t e = cudaMemcpyAsync(c->hctl, c->ctl, sizeof(TeamCtl) * nctl_copy, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->hqerr, c->qerr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "query");
+  const uint32_t q = *c->hqerr;
+  if (q == kErrTimeout) return fail(c, SVV_ETIMEOUT, "a device wait or the round cap expired");
+  if (q != 0) return fail(c, SVV_EINTERNAL, "device capacity check failed");
+  c->err.clear();
+  return SVV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* svv_status_str(svv_status s) {
+  switch (s) {
+    case SVV_OK: return "SVV_OK";
+    case SVV_EINVAL: return "SVV_EINVAL";
+    case SVV_ENOMEM: return "SVV_ENOMEM";
+    case SVV_ECUDA: return "SVV_ECUDA";
+    case SVV_ETIMEOUT: return "SVV_ETIMEOUT";
+    case SVV_EBUSY: return "SVV_EBUSY";
+    case SVV_ENOTLOADED: return "SVV_ENOTLOADED";
+    case SVV_EINTERNAL: return "SVV_EINTERNAL";
+  }
+  return "SVV_UNKNOWN";
+}
+
+const char* svv_last_error(const svv_ctx* c) { return c ? c->err.c_str() : ""; }
+
+uint64_t svv_device_bytes(const svv_ctx* c) { return c ? c->allocated : 0; }
+
+svv_status svv_create(svv_ctx** out, int device, uint64_t budget) {
+  if (!out) return SVV_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SVV_ECUDA;
+  }
+  if (device < 0 || device >= n) return SVV_EINVAL;
+  svv_ctx* c = new (std::nothrow) svv_ctx();
+  if (!c) return SVV_ENOMEM;
+  c->device = device;
+  c->budget = budget;
+  c->budget_auto = budget == 0;
+  DeviceGuard dg(device);
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (!coop || c->num_sms <= 0) {
+    delete c;
+    return SVV_ECUDA;
+  }
+  c->occ_solve = occupancy_solve(c->threads);
+  c->occ_qrs = occupancy_qrs(c->threads);
+  c->occ_relax = occupancy_relax(c->threads);
+  if (c->occ_solve <= 0 || c->occ_qrs <= 0 || c->occ_relax <= 0) {
+    delete c;
+    return SVV_ECUDA;
+  }
+  e = cudaMallocHost((void**)&c->hctl, sizeof(TeamCtl) * kNumCtl);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hqerr, sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    if (c->hctl) cudaFreeHost(c->hctl);
+    delete c;
+    cudaGetLastError();
+    return SVV_ENOMEM;
+  }
+  *out = c;
+  return SVV_OK;
+}
+
+void svv_destroy(svv_ctx* c) {
+  if (!c) return;
+  {
+    DeviceGuard dg(c->device);
+    cudaDeviceSynchronize();
+    free_graph(c);
+    if (c->hctl) cudaFreeHost(c->hctl);
+    if (c->hqerr) cudaFreeHost(c->hqerr);
+    for (auto& e : c->ev)
+      if (e) cudaEventDestroy(e);
+  }
+  delete c;
+}
+
+svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
+  if (!c || !key) return SVV_EINVAL;
+  auto log2_ok = [](int64_t x, int lo, int hi, uint32_t& out) {
+    for (int s = lo; s <= hi; ++s)
+      if (x == (int64_t(1) << s)) {
+        out = (uint32_t)s;
+        return true;
+      }
+    return false;
+  };
+  std::string k(key);
+  if (k == "max_iters") {
+    if (v < 0 || v > 0xFFFFFFF0ll) return fail(c, SVV_EINVAL, "max_iters out of range");
+    c->maxit = (uint32_t)v;
+  } else if (k == "spin_limit_ms") {
+    if (v < 1 || v > 600000) return fail(c, SVV_EINVAL, "spin_limit_ms out of range");
+    c->spin_ms = (uint32_t)v;
+  } else if (k == "solve_chunk") {
+    if (!log2_ok(v, 4, 12, c->solve_cs)) return fail(c, SVV_EINVAL, "solve_chunk: power of two in [16, 4096]");
+  } else if (k == "relax_chunk") {
+    if (!log2_ok(v, 3, 12, c->relax_cs)) return fail(c, SVV_EINVAL, "relax_chunk: power of two in [8, 4096]");
+  } else if (k == "qrs_chunk") {
+    if (!log2_ok(v, 5, 14, c->qrs_cs)) return fail(c, SVV_EINVAL, "qrs_chunk: power of two in [32, 16384]");
+  } else if (k == "phase_timing") {
+    if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "phase_timing is 0 or 1");
+    if (v && !c->ev[0]) {
+      DeviceGuard dg(c->device);
+      for (auto& e : c->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
+    }
+    c->phase_timing = v != 0;
+  } else if (k == "blocks_per_sm") {
+    if (v < 0 || v > 4) return fail(c, SVV_EINVAL, "blocks_per_sm in [0, 4]");
+    c->bps = (int)v;
+  } else {
+    return fail(c, SVV_EINVAL, "unknown tuning key: " + k);
+  }
+  // capacities depend on the chunk sizes: resize on the next load
+  if (c->loaded && (k == "solve_chunk" || k == "relax_chunk" || k == "qrs_chunk")) {
+    const uint64_t need_q = (uint64_t)c->g.V + c->g.E / (1u << std::min(c->solve_cs, c->relax_cs)) + 64;
+    const uint64_t need_u = (uint64_t)c->g.V + c->g.E / (1u << c->qrs_cs) + 64;
+    if (need_q > c->qcap || need_u > c->ucap) {
+      return fail(c, SVV_EINVAL, "chunk smaller than the one the graph was loaded with; set it before svv_load");
+    }
+  }
+  return SVV_OK;
+}
+
+svv_status svv_get_stats(svv_ctx* c, svv_stats* out) {
+  if (!c || !out) return SVV_EINVAL;
+  *out = c->stats;
+  return SVV_OK;
+}
+
+svv_status svv_load(svv_ctx* c, uint32_t V, uint64_t E, uint32_t S, const uint64_t* row_ptr,
+                    const uint32_t* col, const uint32_t* weight, const uint64_t* mask,
+                    int inputs_on_device) {
+  if (!c) return SVV_EINVAL;
+  if (V == 0 || V >= 0xFFFFFFFFu) return fail(c, SVV_EINVAL, "V must be in [1, 2^32-2]");
+  if (S == 0) return fail(c, SVV_EINVAL, "S must be >= 1");
+  if (E >= 0xFFFFFFFFull) return fail(c, SVV_EINVAL, "E must be < 2^32-1");
+  if (!row_ptr || (E && (!col || !weight || !mask))) return fail(c, SVV_EINVAL, "NULL input array");
+  DeviceGuard dg(c->device);
+  const uint32_t W = ceil_div(S, 64);
+
+  // host copies of device inputs
+  std::vector<uint64_t> h_rp, h_mask;
+  std::vector<uint32_t> h_col, h_w;
+  if (inputs_on_device) {
+    h_rp.resize((size_t)V + 1);
+    h_col.resize(E);
+    h_w.resize(E);
+    h_mask.resize((size_t)E * W);
+    cudaError_t e = cudaMemcpy(h_rp.data(), row_ptr, h_rp.size() * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && E) e = cudaMemcpy(h_col.data(), col, E * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && E) e = cudaMemcpy(h_w.data(), weight, E * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && E) e = cudaMemcpy(h_mask.data(), mask, h_mask.size() * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copying device inputs");
+    row_ptr = h_rp.data();
+    col = h_col.data();
+    weight = h_w.data();
+    mask = h_mask.data();
+  }
+  // validate
+  if (row_ptr[0] != 0) return fail(c, SVV_EINVAL, "row_ptr[0] != 0");
+  for (uint32_t v = 0; v < V; ++v)
+    if (row_ptr[v + 1] < row_ptr[v]) return fail(c, SVV_EINVAL, "row_ptr not non-decreasing");
+  if (row_ptr[V] != E) return fail(c, SVV_EINVAL, "row_ptr[V] != E");
+  for (uint64_t e = 0; e < E; ++e)
+    if (col[e] >= V) return fail(c, SVV_EINVAL, "col >= V");
+
+  // classify against the history [0, S): full / partial / absent
+  std::vector<uint64_t> hist(W);
+  for (uint32_t j = 0; j < W; ++j) {
+    const uint32_t n = std::min<uint32_t>(64, S - 64 * j);
+    hist[j] = n == 64 ? ~0ull : ((1ull << n) - 1ull);
+  }
+  std::vector<uint32_t> rp((size_t)V + 1, 0), nfp((size_t)V + 1, 0);
+  std::vector<uint8_t> kind(E);  // 0 absent, 1 full, 2 partial
+  for (uint32_t v = 0; v < V; ++v) {
+    uint32_t nfull = 0, npart = 0;
+    for (uint64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+      bool all = true, any = false;
+      const uint64_t* m = mask + e * W;
+      for (uint32_t j = 0; j < W; ++j) {
+        const uint64_t x = m[j] & hist[j];
+        all &= (x == hist[j]);
+        any |= (x != 0);
+      }
+      kind[e] = all ? 1 : (any ? 2 : 0);
+      nfull += all;
+      npart += (!all && any);
+    }
+    rp[v + 1] = rp[v] + nfull + npart;
+    nfp[v + 1] = nfp[v] + npart;
+  }
+  const uint32_t E2 = rp[V], NF = nfp[V];
+  std::vector<uint2> cw(std::max<uint32_t>(E2, 1)), nfcw(std::max<uint32_t>(NF, 1));
+  std::vector<uint32_t> nfsrc(std::max<uint32_t>(NF, 1));
+  std::vector<uint64_t> nfm((size_t)std::max<uint32_t>(NF, 1) * W);
+  for (uint32_t v = 0; v < V; ++v) {
+    uint32_t pf = rp[v], pn = rp[v + 1] - (nfp[v + 1] - nfp[v]), k = nfp[v];
+    for (uint64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+      if (kind[e] == 1) {
+        cw[pf++] = make_uint2(col[e], weight[e]);
+      } else if (kind[e] == 2) {
+        cw[pn++] = make_uint2(col[e], weight[e]);
+        nfcw[k] = make_uint2(col[e], weight[e]);
+        nfsrc[k] = v;
+        for (uint32_t j = 0; j < W; ++j) nfm[(size_t)k * W + j] = mask[e * W + j] & hist[j];
+        ++k;
+      }
+    }
+  }
+
+  // replace the resident graph
+  cudaDeviceSynchronize();
+  free_graph(c);
+  if (c->budget_auto) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    c->budget = fr > (512ull << 20) ? fr - (512ull << 20) : fr / 2;
+  }
+  DevGraph g{};
+  g.V = V;
+  g.S = S;
+  g.W = W;
+  g.E = E2;
+  g.NF = NF;
+  uint32_t *d_rp, *d_nfp, *d_nfsrc;
+  uint2 *d_cw, *d_nfcw;
+  uint64_t* d_nfm;
+  svv_status st;
+  if ((st = alloc_n(c, c->graph_bufs, (uint64_t)V + 1, &d_rp)) || (st = alloc_n(c, c->graph_bufs, (uint64_t)V + 1, &d_nfp)) ||
+      (st = alloc_n(c, c->graph_bufs, std::max<uint32_t>(E2, 1), &d_cw)) ||
+      (st = alloc_n(c, c->graph_bufs, (uint64_t)std::max<uint32_t>(NF, 1) * W, &d_nfm)) ||
+      (st = alloc_n(c, c->graph_bufs, std::max<uint32_t>(NF, 1), &d_nfsrc)) ||
+      (st = alloc_n(c, c->graph_bufs, std::max<uint32_t>(NF, 1), &d_nfcw))) {
+    free_graph(c);
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(d_rp, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_nfp, nfp.data(), nfp.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_cw, cw.data(), (size_t)E2 * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_nfm, nfm.data(), (size_t)NF * W * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_nfsrc, nfsrc.data(), (size_t)NF * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_nfcw, nfcw.data(), (size_t)NF * 8, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_graph(c);
+    return cuda_fail(c, e, "uploading the graph");
+  }
+  g.rp = d_rp;
+  g.nfp = d_nfp;
+  g.cw = d_cw;
+  g.nfmask = d_nfm;
+  g.nfsrc = d_nfsrc;
+  g.nfcw = d_nfcw;
+
+  // scratch sized from V and E
+  const uint64_t qcap = (uint64_t)V + E2 / (1u << std::min(c->solve_cs, c->relax_cs)) + 64;
+  const uint64_t ucap = (uint64_t)V + E2 / (1u << c->qrs_cs) + 64;
+  if (qcap >= 0xFFFFFFFFull || ucap >= 0xFFFFFFFFull) {
+    free_graph(c);
+    return fail(c, SVV_EINVAL, "graph too large for 32-bit work queues");
+  }
+  const uint64_t nblk = (uint64_t)c->num_sms * 4;
+  if ((st = alloc_n(c, c->scratch_bufs, V, &c->rI)) || (st = alloc_n(c, c->scratch_bufs, V, &c->rU)) ||
+      (st = alloc_n(c, c->scratch_bufs, V, &c->stamp)) || (st = alloc_n(c, c->scratch_bufs, V, &c->row)) ||
+      (st = alloc_n(c, c->scratch_bufs, V, &c->uv)) || (st = alloc_n(c, c->scratch_bufs, 4 * nblk, &c->part)) ||
+      (st = alloc_n(c, c->scratch_bufs, 2ull * V, &c->qcnt)) || (st = alloc_n(c, c->scratch_bufs, 2ull * V, &c->cur)) ||
+      (st = alloc_n(c, c->scratch_bufs, V, &c->qrow)) ||
+      (st = alloc_n(c, c->scratch_bufs, std::max<uint32_t>(E2, 1), &c->qcw)) ||
+      (st = alloc_n(c, c->scratch_bufs, qcap, &c->q0)) || (st = alloc_n(c, c->scratch_bufs, qcap, &c->q1)) ||
+      (st = alloc_n(c, c->scratch_bufs, ucap, &c->units)) ||
+      (st = alloc_n(c, c->scratch_bufs, kNumCtl, &c->ctl)) || (st = alloc_n(c, c->scratch_bufs, 1, &c->qerr))) {
+    free_graph(c);
+    return st;
+  }
+  c->qcap = (uint32_t)qcap;
+  c->ucap = (uint32_t)ucap;
+  c->ecap = std::max<uint32_t>(E2, 1);
+  c->g = g;
+  c->loaded = true;
+  c->stats = svv_stats{};
+  c->err.clear();
+  return SVV_OK;
+}
+
+svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, uint32_t wl, uint32_t* out,
+                     void* stream) {
+  svv_status st = check_query(c, (int)type, source, wb, wl, out);
+  if (st) return st;
+  DeviceGuard dg(c->device);
+  if ((st = ensure_window(c, wl))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(c->ctl, 0, sizeof(TeamCtl) * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->qerr, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+  const int t = (int)type;
+  const bool timing = c->phase_timing;
+  if (timing) cudaEventRecord(c->ev[0], s);
+
+  // a1: intersection graph (edges present in every window snapshot)
+  SolveArgs a1 = solve_base(c, wb, wl);
+  a1.init = kInitSource;
+  a1.source = source;
+  a1.val = c->rI;
+  a1.ctl = c->ctl + 0;
+  a1.skip_nf = (wb == 0 && wl == c->g.S) ? 1 : 0;
+  if ((e = launch_solve(t, kPredAll, a1, cfg_for(c, c->occ_solve), s)) != cudaSuccess)
+    return cuda_fail(c, e, "launch intersection solve");
+  if (timing) cudaEventRecord(c->ev[1], s);
+  // a2: union graph, incrementally from the intersection values
+  SolveArgs a2 = solve_base(c, wb, wl);
+  a2.init = kInitSeed;
+  a2.source = source;
+  a2.base = c->rI;
+  a2.val = c->rU;
+  a2.ctl = c->ctl + 1;
+  if ((e = launch_solve(t, kPredAny, a2, cfg_for(c, c->occ_solve), s)) != cudaSuccess)
+    return cuda_fail(c, e, "launch union solve");
+  if (timing) cudaEventRecord(c->ev[2], s);
+  // a3+a4: stable compaction and the Q-relevant subgraph
+  QrsArgs q{};
+  q.g = c->g;
+  q.win = Window{wb, wl};
+  q.QW = ceil_div(wl, 64);
+  q.rI = c->rI;
+  q.rU = c->rU;
+  q.row = c->row;
+  q.uv = c->uv;
+  q.part = c->part;
+  q.units = c->units;
+  q.ucap = c->ucap;
+  q.cshift = c->qrs_cs;
+  q.qcnt = c->qcnt;
+  q.qrow = c->qrow;
+  q.cur = c->cur;
+  q.qcw = c->qcw;
+  q.qmask = c->qmask;
+  q.ecap = c->ecap;
+  q.mcap = c->mcap;
+  q.ctl = c->ctl + 2;
+  q.qerr = c->qerr;
+  q.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
+  LaunchCfg qc = cfg_for(c, c->occ_qrs);
+  if ((int64_t)qc.blocks > (int64_t)c->num_sms * 4) qc.blocks = c->num_sms * 4;
+  if ((e = launch_qrs(q, qc, s)) != cudaSuccess) return cuda_fail(c, e, "launch subgraph extraction");
+  if (timing) cudaEventRecord(c->ev[3], s);
+  float ms_relax = 0.f, ms_scatter = 0.f;
+  // a5+a6 per slab of at most 128 snapshots (a window longer than that is
+  // relaxed slab by slab over the same subgraph; snapshots are independent)
+  for (uint32_t s0 = 0; s0 < wl; s0 += kMaxSlab) {
+    const uint32_t ls = std::min(kMaxSlab, wl - s0);
+    uint32_t P, K;
+    slab_shape(ls, P, K);
+    if (s0 > 0 && (e = cudaMemsetAsync(c->ctl + 3, 0, sizeof(TeamCtl), s)) != cudaSuccess)
+      return cuda_fail(c, e, "memset");
+    if (timing) cudaEventRecord(c->ev[6], s);
+    RelaxArgs r{};
+    r.g = c->g;
+    r.win = Window{wb, wl};
+    r.s0 = s0;
+    r.ls = ls;
+    r.QW = q.QW;
+    r.rI = c->rI;
+    r.row = c->row;
+    r.uv = c->uv;
+    r.qrow = c->qrow;
+    r.qcw = c->qcw;
+    r.qmask = c->qmask;
+    r.counts = &(c->ctl + 2)->aux[0];
+    r.val = c->val;
+    r.LP = P * K;
+    r.stamp = c->stamp;
+    r.q0 = c->q0;
+    r.q1 = c->q1;
+    r.qcap = c->qcap;
+    r.cshift = c->relax_cs;
+    r.ctl = c->ctl + 3;
+    r.qerr = c->qerr;
+    r.maxit = c->maxit ? c->maxit : c->g.V + 2u;
+    r.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
+    if ((e = launch_relax(t, P, K, r, cfg_for(c, c->occ_relax), s)) != cudaSuccess)
+      return cuda_fail(c, e, "launch relaxation");
+    if (timing) cudaEventRecord(c->ev[4], s);
+    ScatterArgs sa{};
+    sa.V = c->g.V;
+    sa.s0 = s0;
+    sa.ls = ls;
+    sa.rI = c->rI;
+    sa.row = c->row;
+    sa.val = c->val;
+    sa.LP = P * K;
+    sa.out = out;
+    sa.qerr = c->qerr;
+    if ((e = launch_scatter(sa, s)) != cudaSuccess) return cuda_fail(c, e, "launch scatter");
+    if (timing) {
+      cudaEventRecord(c->ev[5], s);
+      if (wl > kMaxSlab) {  // several slabs: accumulate per slab
+        float a = 0.f, b = 0.f;
+        cudaEventSynchronize(c->ev[5]);
+        cudaEventElapsedTime(&a, c->ev[6], c->ev[4]);
+        cudaEventElapsedTime(&b, c->ev[4], c->ev[5]);
+        ms_relax += a;
+        ms_scatter += b;
+      }
+    }
+  }
+  st = finish(c, s, 4);
+  svv_stats& S = c->stats;
+  S = svv_stats{};
+  S.unstable = c->hctl[2].aux[0];
+  S.qrs_edges = c->hctl[2].aux[2];
+  S.qrs_masked = c->hctl[2].aux[3];
+  S.iters_cap = c->hctl[0].iters;
+  S.iters_cup = c->hctl[1].iters;
+  S.iters_relax = c->hctl[3].iters;  // last slab
+  S.edges_relaxed_cap = c->hctl[0].relaxed;
+  S.edges_relaxed_cup = c->hctl[1].relaxed;
+  S.edges_relaxed_multi = c->hctl[3].relaxed;
+  if (timing && st == SVV_OK) {
+    S.phase_timing = 1;
+    cudaEventElapsedTime(&S.ms_cap, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&S.ms_cup, c->ev[1], c->ev[2]);
+    cudaEventElapsedTime(&S.ms_qrs, c->ev[2], c->ev[3]);
+    if (wl > kMaxSlab) {
+      S.ms_relax = ms_relax;
+      S.ms_scatter = ms_scatter;
+    } else {
+      cudaEventElapsedTime(&S.ms_relax, c->ev[3], c->ev[4]);
+      cudaEventElapsedTime(&S.ms_scatter, c->ev[4], c->ev[5]);
+    }
+  }
+  return st;
+}
+
+svv_status svv_query_plain(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, uint32_t wl,
+                           uint32_t* out, void* stream) {
+  svv_status st = check_query(c, (int)type, source, wb, wl, out);
+  if (st) return st;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t nslot = std::min<uint32_t>(wl, kNumCtl - 8);
+  cudaError_t e = cudaMemsetAsync(c->ctl + 8, 0, sizeof(TeamCtl) * nslot, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->qerr, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+  const bool timing = c->phase_timing;
+  if (timing) cudaEventRecord(c->ev[0], s);
+  for (uint32_t i = 0; i < wl; ++i) {
+    TeamCtl* slot = c->ctl + 8 + (i % (kNumCtl - 8));
+    if (i >= (uint32_t)(kNumCtl - 8) && (e = cudaMemsetAsync(slot, 0, sizeof(TeamCtl), s)) != cudaSuccess)
+      return cuda_fail(c, e, "memset");
+    SolveArgs a = solve_base(c, wb, wl);
+    a.init = kInitSource;
+    a.source = source;
+    a.bit = wb + i;
+    a.val = out + (size_t)i * c->g.V;
+    a.ctl = slot;
+    if ((e = launch_solve((int)type, kPredBit, a, cfg_for(c, c->occ_solve), s)) != cudaSuccess)
+      return cuda_fail(c, e, "launch per-snapshot solve");
+  }
+  if (timing) cudaEventRecord(c->ev[1], s);
+  st = finish(c, s, 8 + nslot);
+  svv_stats& S = c->stats;
+  S = svv_stats{};
+  if (timing && st == SVV_OK) {
+    S.phase_timing = 1;
+    cudaEventElapsedTime(&S.ms_cap, c->ev[0], c->ev[1]);
+  }
+  for (uint32_t i = 0; i < nslot; ++i) {
+    S.iters_plain_max = std::max(S.iters_plain_max, c->hctl[8 + i].iters);
+    S.edges_relaxed_cap += c->hctl[8 + i].relaxed;
+  }
+  return st;
+}
+
+svv_status svv_get_bounds(svv_ctx* c, uint32_t* cap, uint32_t* cup, uint32_t* row, void* stream) {
+  if (!c) return SVV_EINVAL;
+  if (!c->loaded) return fail(c, SVV_ENOTLOADED, "no graph loaded");
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)c->g.V * sizeof(uint32_t);
+  cudaError_t e = cudaSuccess;
+  if (cap) e = cudaMemcpyAsync(cap, c->rI, n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && cup) e = cudaMemcpyAsync(cup, c->rU, n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && row) e = cudaMemcpyAsync(row, c->row, n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copying bounds");
+  return SVV_OK;
+}
+
+svv_status svv_query_host(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, uint32_t wl,
+                          uint32_t* out_host, void* stream) {
+  svv_status st = check_query(c, (int)type, source, wb, wl, out_host);
+  if (st) return st;
+  DeviceGuard dg(c->device);
+  const uint64_t need = (uint64_t)wl * c->g.V;
+  if (need > c->staging_cap) {
+    if (c->staging) {
+      auto it = std::find(c->scratch_bufs.begin(), c->scratch_bufs.end(), (void*)c->staging);
+      if (it != c->scratch_bufs.end()) c->scratch_bufs.erase(it);
+      cudaFree(c->staging);
+      c->allocated -= ((c->staging_cap * 4 + 255) & ~uint64_t(255));
+      c->staging = nullptr;
+      c->staging_cap = 0;
+    }
+    if ((st = alloc_n(c, c->scratch_bufs, need, &c->staging))) return st;
+    c->staging_cap = need;
+  }
+  st = svv_query(c, type, source, wb, wl, c->staging, stream);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(out_host, c->staging, need * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copying the result to the host");
+  return SVV_OK;
+}
+
+}  // extern "C"

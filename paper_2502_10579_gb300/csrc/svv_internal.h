@@ -1,0 +1,157 @@
+// svv_internal.h -- structures shared by the host orchestration and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace svv {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;  // "no row": the vertex is stable
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+constexpr uint32_t kSat = 0xFFFFFFFEu;   // SSSP sums saturate here
+
+// error codes written by kernels; numerically equal to svv_status values
+enum : uint32_t { kErrNone = 0, kErrTimeout = 4, kErrInternal = 7 };
+
+enum Pred : int { kPredAll = 0, kPredAny = 1, kPredBit = 2 };
+enum Init : int { kInitSource = 0, kInitSeed = 1 };
+
+// Control block of one team of CTAs (one cooperative launch, or one slice of
+// it).  Fields live on separate 128-byte lines so the barrier counter does not
+// share a line with the counters that every warp hits.
+struct alignas(128) TeamCtl {
+  unsigned int bar_count;
+  unsigned int pad0[31];
+  unsigned int bar_gen;
+  unsigned int pad1[31];
+  unsigned int qn[3];      // frontier sizes, a ring over rounds
+  unsigned int pad2[29];
+  unsigned int ticket[3];  // work tickets, a ring over rounds
+  unsigned int pad3[29];
+  unsigned int err;        // kErr* of this team
+  unsigned int iters;      // rounds completed
+  unsigned int aux[14];    // phase outputs (counts), see the kernels
+  unsigned long long relaxed;  // edges examined (diagnostic)
+  unsigned long long pad4[8];
+};
+static_assert(sizeof(TeamCtl) % 128 == 0, "TeamCtl must be cache-line sized");
+
+// Resident versioned graph (Section 4.1 layout, reordered at load):
+// row v holds edges [rp[v], rp[v+1]); the first (rp[v+1]-rp[v]) -
+// (nfp[v+1]-nfp[v]) of them are present in all S snapshots and carry no
+// mask; the rest ("non-full") have W mask words at nfmask[(nfp[v]+j)*W].
+// The non-full edges are also kept as a coordinate list (nfsrc, nfcw) in the
+// same order, for the seeding passes.
+struct DevGraph {
+  uint32_t V, S, W;
+  uint32_t E, NF;
+  const uint32_t* rp;       // [V+1]
+  const uint32_t* nfp;      // [V+1]
+  const uint2* cw;          // [E] (target, weight)
+  const uint64_t* nfmask;   // [NF*W]
+  const uint32_t* nfsrc;    // [NF]
+  const uint2* nfcw;        // [NF]
+};
+
+struct Window {
+  uint32_t b, l;  // snapshots [b, b+l)
+};
+
+struct SolveArgs {
+  DevGraph g;
+  Window win;
+  uint32_t bit;      // kPredBit: the snapshot tested
+  uint32_t source;
+  int init;          // kInit*
+  int skip_nf;       // kPredAll over [0,S): non-full edges can never pass
+  const uint32_t* base;  // kInitSeed: starting values (the intersection-graph solve)
+  uint32_t* val;     // [V] result
+  uint32_t* stamp;   // [V] round in which a vertex was last queued
+  unsigned long long* q0;  // work units: vertex | chunk << 32
+  unsigned long long* q1;
+  uint32_t qcap;
+  uint32_t cshift;   // edges per unit = 1 << cshift
+  TeamCtl* ctl;
+  uint32_t* qerr;    // query-wide error word
+  uint32_t maxit;
+  unsigned long long spin_ns;
+};
+
+struct QrsArgs {
+  DevGraph g;
+  Window win;
+  uint32_t QW;            // mask words per relaxation edge: ceil(win.l / 64)
+  const uint32_t* rI;     // intersection-graph values
+  const uint32_t* rU;     // union-graph values
+  uint32_t* row;          // [V] vertex -> row, kNone if stable
+  uint32_t* uv;           // [V] row -> vertex
+  uint32_t* part;         // [4 * gridDim] per-CTA partial sums
+  unsigned long long* units;  // row | chunk << 32 over unstable rows
+  uint32_t ucap;
+  uint32_t cshift;
+  uint32_t* qcnt;         // [2V] per row: (#all-window edges, #other edges)
+  uint4* qrow;            // [V] per row: {start, all-window end, mask base, end}
+  uint32_t* cur;          // [2V] fill cursors
+  uint2* qcw;             // [E] (target row, weight)
+  uint64_t* qmask;        // [NF*QW] window-rebased masks
+  uint32_t ecap;
+  unsigned long long mcap;  // words
+  TeamCtl* ctl;           // aux[0]=U, aux[1]=#units, aux[2]=E_Q, aux[3]=#masked
+  uint32_t* qerr;
+  unsigned long long spin_ns;
+};
+
+struct RelaxArgs {
+  DevGraph g;
+  Window win;
+  uint32_t s0, ls;        // snapshot slab [win.b+s0, win.b+s0+ls) of this pass
+  uint32_t QW;
+  const uint32_t* rI;
+  const uint32_t* row;
+  const uint32_t* uv;
+  const uint4* qrow;
+  const uint2* qcw;
+  const uint64_t* qmask;
+  const unsigned int* counts;  // qrs team aux: [0]=U
+  uint32_t* val;          // [U * LP]
+  uint32_t LP;            // row stride of val (>= ls)
+  uint32_t* stamp;        // [V]
+  unsigned long long* q0;
+  unsigned long long* q1;
+  uint32_t qcap;
+  uint32_t cshift;
+  TeamCtl* ctl;
+  uint32_t* qerr;
+  uint32_t maxit;
+  unsigned long long spin_ns;
+};
+
+struct ScatterArgs {
+  uint32_t V;
+  uint32_t s0, ls;
+  const uint32_t* rI;
+  const uint32_t* row;
+  const uint32_t* val;
+  uint32_t LP;
+  uint32_t* out;          // [win.l * V]; rows s0.. of this pass
+  const uint32_t* qerr;
+};
+
+// launch helpers (defined in the .cu files)
+struct LaunchCfg {
+  int blocks;     // cooperative grid size
+  int threads;
+};
+
+cudaError_t launch_solve(int type, int pred, const SolveArgs& a, LaunchCfg cfg, cudaStream_t s);
+cudaError_t launch_qrs(const QrsArgs& a, LaunchCfg cfg, cudaStream_t s);
+cudaError_t launch_relax(int type, uint32_t P, uint32_t K, const RelaxArgs& a, LaunchCfg cfg,
+                         cudaStream_t s);
+cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
+
+// occupancy of each cooperative kernel: max resident CTAs per SM at `threads`
+int occupancy_solve(int threads);
+int occupancy_qrs(int threads);
+int occupancy_relax(int threads);
+
+}  // namespace svv

@@ -1,0 +1,292 @@
+// svv_relax.cu -- concurrent relaxation of every window snapshot over the
+// Q-relevant subgraph (Section 4.2, Algorithm 2), and the output scatter.
+//
+// Values are kept vertex-major: row r of `val` holds the LP values of unstable
+// vertex uv[r], one per snapshot of the slab, so one out-edge of a frontier
+// vertex touches one contiguous run of the target's values.  A group of P
+// lanes owns one work unit (row, chunk of edges); lane gl of the group holds
+// snapshots gl, gl+P, ... (K of them).  The group loads P edges at once, then
+// broadcasts them one by one; each lane relaxes its snapshots whose bit is set
+// in the edge's mask (edge ownership, Section 4.2).  The frontier is
+// snapshot-oblivious: a row is queued once per round if any of its snapshots
+// improved.
+//
+// Round 0 initialises every row to the intersection-graph value (Algorithm 2
+// "R_i = R_QRS") and seeds from the addition edges whose sink is unstable
+// (Algorithm 2 addition batches; Section 3 Step 4 drops those with a stable
+// sink).  The seeding reads the resident list of edges that are not present in
+// all snapshots; an edge present in every window snapshot belongs to the
+// intersection graph, whose values are already a fixed point on it, so it is
+// skipped.  Sources of seed edges hold their intersection-graph value in every
+// snapshot at that point.
+#include "svv_device.cuh"
+#include "svv_push.cuh"
+
+namespace svv {
+
+constexpr int kRelaxThreads = 512;
+
+template <class Op, int P, int K>
+__global__ void __launch_bounds__(kRelaxThreads) relax_kernel(RelaxArgs a) {
+  const DevGraph& g = a.g;
+  TeamCtl* c = a.ctl;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned nthreads = gridDim.x * blockDim.x;
+  const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned gwarp = gtid >> 5, nwarps = nthreads >> 5;
+  if (ld_acquire(a.qerr) != 0u) return;
+  const uint32_t U = a.counts[0];
+  const uint32_t LP = a.LP;
+  const uint32_t lps = __ffs(LP) - 1;  // LP is a power of two
+  const uint32_t snap0 = a.win.b + a.s0;  // absolute snapshot of slab column 0
+
+  // ---- round 0a: values and stamps
+  const unsigned long long nval = (unsigned long long)U << lps;
+  for (unsigned long long idx = gtid; idx < nval; idx += nthreads)
+    a.val[idx] = a.rI[a.uv[(uint32_t)(idx >> lps)]];
+  for (uint32_t r = gtid; r < U; r += nthreads) a.stamp[r] = 0u;
+  if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
+
+  // ---- round 0b: seed from addition edges with an unstable sink
+  for (uint32_t k0 = gwarp * 32u; k0 < g.NF; k0 += nwarps * 32u) {
+    const uint32_t k = k0 + lane;
+    bool qual = false;
+    if (k < g.NF) {
+      const uint32_t rx = a.row[__ldg(&g.nfcw[k].x)];
+      if (rx != kNone) {
+        bool any, all;
+        window_any_all(g.nfmask + (size_t)k * g.W, a.win, any, all);
+        qual = any && !all;
+      }
+    }
+    unsigned bq = __ballot_sync(kFullMask, qual);
+    while (bq) {
+      const uint32_t kj = k0 + (__ffs(bq) - 1);
+      bq &= bq - 1u;
+      const uint2 e = __ldg(g.nfcw + kj);
+      const uint32_t rx = a.row[e.x];
+      const uint32_t cand = Op::relax(a.rI[__ldg(g.nfsrc + kj)], e.y);
+      const uint64_t* m = g.nfmask + (size_t)kj * g.W;
+      bool imp = false;
+      for (uint32_t i = lane; i < a.ls; i += 32u) {
+        if (mask_bit(m, snap0 + i)) {
+          uint32_t* p = a.val + ((size_t)rx << lps) + i;
+          if (Op::better(cand, ld_cg(p))) {
+            const uint32_t old = Op::atomic(p, cand);
+            imp |= Op::better(cand, old);
+          }
+        }
+      }
+      const bool any_imp = __any_sync(kFullMask, imp);
+      bool push = false;
+      uint32_t deg = 0;
+      if (any_imp && lane == 0 && atomicExch(a.stamp + rx, 1u) != 1u) {
+        push = true;
+        const uint4 d = a.qrow[rx];
+        deg = d.w - d.x;
+      }
+      warp_push_units(push, rx, deg, a.cshift, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
+    }
+  }
+  if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
+
+  // ---- rounds >= 1: Algorithm 2 while-loop over the frontier
+  constexpr int G = 32 / P;
+  const unsigned grp = lane / P, gl = lane % P;
+  const unsigned gmask = (P == 32) ? kFullMask : (((1u << P) - 1u) << (grp * P));
+  unsigned long long relaxed = 0;
+  uint32_t it = 1;
+  for (;; ++it) {
+    const uint32_t cur = it % 3u, nxt = (it + 1u) % 3u, clr = (it + 2u) % 3u;
+    uint32_t n = ld_acquire(&c->qn[cur]);
+    if (n == 0u) break;
+    if (it > a.maxit) {
+      if (gtid == 0) set_err(c, a.qerr, kErrTimeout);
+      break;
+    }
+    n = min(n, a.qcap);
+    if (gtid == 0) {
+      atomicExch(&c->qn[clr], 0u);
+      atomicExch(&c->ticket[clr], 0u);
+    }
+    const unsigned long long* qin = (it & 1u) ? a.q1 : a.q0;
+    unsigned long long* qout = (it & 1u) ? a.q0 : a.q1;
+    unsigned* qn_out = &c->qn[nxt];
+    const uint32_t stamp_next = it + 1u;
+
+    for (;;) {
+      uint32_t t0 = 0;
+      if (lane == 0) t0 = atomicAdd(&c->ticket[cur], (unsigned)G);
+      t0 = __shfl_sync(kFullMask, t0, 0);
+      if (t0 >= n) break;
+      const uint32_t ui = t0 + grp;
+      uint32_t beg = 0, end = 0, fe = 0, nfb = 0;
+      uint32_t sv[K];
+#pragma unroll
+      for (int kk = 0; kk < K; ++kk) sv[kk] = Op::kIdentity;
+      if (ui < n) {
+        const unsigned long long u = ld_cg(qin + ui);
+        const uint32_t r = (uint32_t)u, ch = (uint32_t)(u >> 32);
+        const uint4 d = a.qrow[r];
+        beg = d.x + (ch << a.cshift);
+        end = min(d.w, beg + (1u << a.cshift));
+        fe = d.y;
+        nfb = d.z;
+        const uint32_t* src = a.val + ((size_t)r << lps) + gl;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) sv[kk] = ld_cg(src + kk * P);
+      }
+      const uint32_t cnt = end > beg ? end - beg : 0u;
+      const uint32_t maxcnt = __reduce_max_sync(kFullMask, cnt);
+      if (gl == 0) relaxed += cnt;
+      for (uint32_t j0 = 0; j0 < maxcnt; j0 += P) {
+        const uint32_t e = beg + j0 + gl;
+        uint32_t xr = 0, w = 0;
+        uint64_t m0 = ~0ull, m1 = ~0ull;
+        if (e < end) {
+          const uint2 ew = a.qcw[e];
+          xr = ew.x;
+          w = ew.y;
+          if (e >= fe) {
+            const uint64_t* mp = a.qmask + (size_t)(nfb + (e - fe)) * a.QW;
+            m0 = mask_extract(mp, a.QW, a.s0);
+            if (P * K > 64) m1 = mask_extract(mp, a.QW, a.s0 + 64u);
+          }
+        }
+        bool pend = false;
+        uint32_t pend_x = 0;
+        const uint32_t nj = min((uint32_t)P, maxcnt - j0);
+        for (uint32_t jj = 0; jj < nj; ++jj) {
+          const uint32_t ex = __shfl_sync(kFullMask, xr, jj, P);
+          const uint32_t ew = __shfl_sync(kFullMask, w, jj, P);
+          const uint64_t em0 = __shfl_sync(kFullMask, m0, jj, P);
+          uint64_t em1 = ~0ull;
+          if (P * K > 64) em1 = __shfl_sync(kFullMask, m1, jj, P);
+          const bool ev = (beg + j0 + jj) < end;
+          bool imp = false;
+          if (ev) {
+            uint32_t* row = a.val + ((size_t)ex << lps) + gl;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+              const uint32_t i = gl + kk * P;
+              const bool bit = (i < 64u) ? ((em0 >> i) & 1ull) : ((em1 >> (i - 64u)) & 1ull);
+              if (i < a.ls && bit) {
+                const uint32_t cand = Op::relax(sv[kk], ew);
+                if (Op::better(cand, ld_cg(row + kk * P))) {
+                  const uint32_t old = Op::atomic(row + kk * P, cand);
+                  imp |= Op::better(cand, old);
+                }
+              }
+            }
+          }
+          const unsigned bi = __ballot_sync(kFullMask, imp) & gmask;
+          if (gl == jj && bi) {
+            pend = true;
+            pend_x = ex;
+          }
+        }
+        bool push = false;
+        uint32_t deg = 0;
+        if (pend && atomicExch(a.stamp + pend_x, stamp_next) != stamp_next) {
+          push = true;
+          const uint4 d = a.qrow[pend_x];
+          deg = d.w - d.x;
+        }
+        warp_push_units(push, pend_x, deg, a.cshift, qout, qn_out, a.qcap, c, a.qerr, lane);
+      }
+    }
+    if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
+  }
+  if (gl == 0 && relaxed) atomicAdd(&c->relaxed, relaxed);
+  if (gtid == 0) c->iters = it - 1u;
+}
+
+// ---------------------------------------------------------------------------
+// Output scatter: out[(s0+i)*V + v] = intersection value if v is stable, else
+// the relaxed value of its row.  A CTA stages a tile of kTV vertices x ls
+// snapshots in shared memory so both the row reads and the snapshot-major
+// writes are coalesced.
+constexpr int kTV = 64;
+constexpr int kScatterThreads = 256;
+
+__global__ void __launch_bounds__(kScatterThreads) scatter_kernel(ScatterArgs a) {
+  extern __shared__ uint32_t tile[];  // [ls][kTV + 1]
+  if (*a.qerr != 0u) return;
+  const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t v0 = blockIdx.x * kTV;
+  const uint32_t lps = __ffs(a.LP) - 1;
+  for (uint32_t t = wid; t < (uint32_t)kTV; t += nw) {
+    const uint32_t v = v0 + t;
+    if (v >= a.V) break;
+    const uint32_t r = a.row[v];
+    if (r == kNone) {
+      const uint32_t x = a.rI[v];
+      for (uint32_t i = lane; i < a.ls; i += 32u) tile[i * (kTV + 1) + t] = x;
+    } else {
+      const uint32_t* src = a.val + ((size_t)r << lps);
+      for (uint32_t i = lane; i < a.ls; i += 32u) tile[i * (kTV + 1) + t] = src[i];
+    }
+  }
+  __syncthreads();
+  const uint32_t nv = min((uint32_t)kTV, a.V - v0);
+  for (uint32_t idx = threadIdx.x; idx < a.ls * (uint32_t)kTV; idx += blockDim.x) {
+    const uint32_t i = idx / kTV, t = idx % kTV;
+    if (t < nv) a.out[(size_t)(a.s0 + i) * a.V + v0 + t] = tile[i * (kTV + 1) + t];
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <class Op, int P, int K>
+static cudaError_t launch_r(const RelaxArgs& a, LaunchCfg cfg, cudaStream_t s) {
+  RelaxArgs copy = a;
+  void* args[] = {&copy};
+  return cudaLaunchCooperativeKernel((const void*)relax_kernel<Op, P, K>, dim3(cfg.blocks),
+                                     dim3(cfg.threads), args, 0, s);
+}
+
+template <class Op>
+static cudaError_t launch_pk(uint32_t P, uint32_t K, const RelaxArgs& a, LaunchCfg cfg, cudaStream_t s) {
+  if (P == 8) return launch_r<Op, 8, 1>(a, cfg, s);
+  if (P == 16) return launch_r<Op, 16, 1>(a, cfg, s);
+  if (K == 1) return launch_r<Op, 32, 1>(a, cfg, s);
+  if (K == 2) return launch_r<Op, 32, 2>(a, cfg, s);
+  return launch_r<Op, 32, 4>(a, cfg, s);
+}
+
+cudaError_t launch_relax(int type, uint32_t P, uint32_t K, const RelaxArgs& a, LaunchCfg cfg,
+                         cudaStream_t s) {
+  switch (type) {
+    case 0: return launch_pk<OpSSSP>(P, K, a, cfg, s);
+    case 1: return launch_pk<OpSSWP>(P, K, a, cfg, s);
+    default: return launch_pk<OpBFS>(P, K, a, cfg, s);
+  }
+}
+
+cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
+  const uint32_t blocks = (a.V + kTV - 1) / kTV;
+  const size_t smem = (size_t)a.ls * (kTV + 1) * sizeof(uint32_t);
+  scatter_kernel<<<blocks, kScatterThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class Op>
+static int occ_op(int threads) {
+  const void* ks[] = {(const void*)relax_kernel<Op, 8, 1>, (const void*)relax_kernel<Op, 16, 1>,
+                      (const void*)relax_kernel<Op, 32, 1>, (const void*)relax_kernel<Op, 32, 2>,
+                      (const void*)relax_kernel<Op, 32, 4>};
+  int best = 1 << 30;
+  for (const void* k : ks) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, 0) != cudaSuccess) return 0;
+    best = n < best ? n : best;
+  }
+  return best;
+}
+
+int occupancy_relax(int threads) {
+  int a = occ_op<OpSSSP>(threads), b = occ_op<OpSSWP>(threads), c = occ_op<OpBFS>(threads);
+  int m = a < b ? a : b;
+  return m < c ? m : c;
+}
+
+}  // namespace svv

@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libsvv's C ABI (include/svv.h).
+
+Functions keep the C names and only marshal arguments: every step of a query
+runs in the library's CUDA kernels.  Importing this module never falls back to
+anything: if ``libsvv.so`` is missing, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+SVV_SSSP, SVV_SSWP, SVV_BFS = 0, 1, 2
+STATUS = {0: "SVV_OK", 1: "SVV_EINVAL", 2: "SVV_ENOMEM", 3: "SVV_ECUDA", 4: "SVV_ETIMEOUT",
+          5: "SVV_EBUSY", 6: "SVV_ENOTLOADED", 7: "SVV_EINTERNAL"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsvv.so")
+
+# every symbol include/svv.h declares
+EXPORTS = ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "svv_query_plain",
+           "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats", "svv_device_bytes", "svv_status_str",
+           "svv_last_error", "svv_destroy")
+
+
+class SvvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class svv_stats(ctypes.Structure):
+    _fields_ = [("unstable", ctypes.c_uint32), ("qrs_edges", ctypes.c_uint32),
+                ("qrs_masked", ctypes.c_uint32), ("iters_cap", ctypes.c_uint32),
+                ("iters_cup", ctypes.c_uint32), ("iters_relax", ctypes.c_uint32),
+                ("iters_plain_max", ctypes.c_uint32), ("phase_timing", ctypes.c_uint32),
+                ("edges_relaxed_cap", ctypes.c_uint64), ("edges_relaxed_cup", ctypes.c_uint64),
+                ("edges_relaxed_multi", ctypes.c_uint64), ("ms_cap", ctypes.c_float),
+                ("ms_cup", ctypes.c_float), ("ms_qrs", ctypes.c_float), ("ms_relax", ctypes.c_float),
+                ("ms_scatter", ctypes.c_float), ("reserved", ctypes.c_float)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsvv.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, u32, u64, i32, i64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_int64
+    L.svv_create.argtypes = [ctypes.POINTER(P), i32, u64]
+    L.svv_build_versioned_csr.argtypes = [u32, u32, u64, P, P, P, P, P, P, P, P, P, ctypes.POINTER(u64)]
+    L.svv_load.argtypes = [P, u32, u64, u32, P, P, P, P, i32]
+    q = [P, i32, u32, u32, u32, P, P]
+    L.svv_query.argtypes = q
+    L.svv_query_plain.argtypes = q
+    L.svv_query_host.argtypes = q
+    L.svv_get_bounds.argtypes = [P, P, P, P, P]
+    L.svv_set_tuning.argtypes = [P, ctypes.c_char_p, i64]
+    L.svv_get_stats.argtypes = [P, ctypes.POINTER(svv_stats)]
+    L.svv_device_bytes.argtypes = [P]
+    L.svv_device_bytes.restype = u64
+    L.svv_status_str.argtypes = [i32]
+    L.svv_status_str.restype = ctypes.c_char_p
+    L.svv_last_error.argtypes = [P]
+    L.svv_last_error.restype = ctypes.c_char_p
+    L.svv_destroy.argtypes = [P]
+    L.svv_destroy.restype = None
+    for f in ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "svv_query_plain",
+              "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats"):
+        getattr(L, f).restype = i32
+    _lib = L
+    return L
+
+
+def _check(ctx, st: int):
+    if st != 0:
+        msg = lib().svv_last_error(ctx).decode() if ctx else ""
+        raise SvvError(st, msg)
+
+
+def _ptr(x):
+    """Address of a numpy array or a torch tensor."""
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# --------------------------------------------------------------------------
+# C-ABI mirrors
+def svv_create(device: int = 0, hbm_budget_bytes: int = 0):
+    h = ctypes.c_void_p()
+    _check(None, lib().svv_create(ctypes.byref(h), device, hbm_budget_bytes))
+    return h
+
+
+def svv_destroy(ctx):
+    lib().svv_destroy(ctx)
+
+
+def svv_status_str(st: int) -> str:
+    return lib().svv_status_str(st).decode()
+
+
+def svv_last_error(ctx) -> str:
+    return lib().svv_last_error(ctx).decode()
+
+
+def svv_device_bytes(ctx) -> int:
+    return int(lib().svv_device_bytes(ctx))
+
+
+def svv_set_tuning(ctx, key: str, value: int):
+    _check(ctx, lib().svv_set_tuning(ctx, key.encode(), int(value)))
+
+
+def svv_get_stats(ctx) -> dict:
+    s = svv_stats()
+    _check(ctx, lib().svv_get_stats(ctx, ctypes.byref(s)))
+    return {name: (float(getattr(s, name)) if name.startswith("ms_") else int(getattr(s, name)))
+            for name, _ in svv_stats._fields_ if name != "reserved"}
+
+
+def svv_build_versioned_csr(V: int, S: int, src, dst, w, t_add, t_del):
+    """Host builder: edge instances with live interval [t_add, t_del) ->
+    (row_ptr u64[V+1], col u32[E], weight u32[E], mask u64[E*W])."""
+    src = np.ascontiguousarray(src, np.uint32)
+    dst = np.ascontiguousarray(dst, np.uint32)
+    w = np.ascontiguousarray(w, np.uint32)
+    t_add = np.ascontiguousarray(t_add, np.uint32)
+    t_del = np.ascontiguousarray(t_del, np.uint32)
+    n = src.shape[0]
+    W = (S + 63) // 64
+    row_ptr = np.empty(V + 1, np.uint64)
+    col = np.empty(max(n, 1), np.uint32)
+    weight = np.empty(max(n, 1), np.uint32)
+    mask = np.empty(max(n, 1) * W, np.uint64)
+    E = ctypes.c_uint64()
+    _check(None, lib().svv_build_versioned_csr(V, S, n, _ptr(src), _ptr(dst), _ptr(w), _ptr(t_add),
+                                               _ptr(t_del), _ptr(row_ptr), _ptr(col), _ptr(weight),
+                                               _ptr(mask), ctypes.byref(E)))
+    E = int(E.value)
+    return row_ptr, col[:E], weight[:E], mask[:E * W]
+
+
+def svv_load(ctx, V: int, E: int, S: int, row_ptr, col, weight, mask, inputs_on_device: bool = False):
+    _check(ctx, lib().svv_load(ctx, V, E, S, _ptr(row_ptr), _ptr(col), _ptr(weight), _ptr(mask),
+                               1 if inputs_on_device else 0))
+
+
+def svv_query(ctx, qtype: int, source: int, win_begin: int, win_len: int, out, stream=None):
+    _check(ctx, lib().svv_query(ctx, qtype, source, win_begin, win_len, _ptr(out), _stream(stream)))
+
+
+def svv_query_plain(ctx, qtype: int, source: int, win_begin: int, win_len: int, out, stream=None):
+    _check(ctx, lib().svv_query_plain(ctx, qtype, source, win_begin, win_len, _ptr(out), _stream(stream)))
+
+
+def svv_query_host(ctx, qtype: int, source: int, win_begin: int, win_len: int, out_host, stream=None):
+    _check(ctx, lib().svv_query_host(ctx, qtype, source, win_begin, win_len, _ptr(out_host),
+                                     _stream(stream)))
+
+
+def svv_get_bounds(ctx, cap=None, cup=None, row=None, stream=None):
+    n = ctypes.c_void_p(0)
+    _check(ctx, lib().svv_get_bounds(ctx, _ptr(cap) if cap is not None else n,
+                                     _ptr(cup) if cup is not None else n,
+                                     _ptr(row) if row is not None else n, _stream(stream)))
+
+
+# --------------------------------------------------------------------------
+@dataclass
+class LoadedGraph:
+    V: int
+    S: int
+    E: int
+
+
+class Context:
+    """Owns one svv context; convenience over the C-ABI mirrors above."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.device = device
+        self.h = svv_create(device, hbm_budget_bytes)
+        self.graph = None
+
+    def close(self):
+        if self.h is not None:
+            svv_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_log(self, log) -> LoadedGraph:
+        """Build the versioned union graph of an edge log and load it."""
+        rp, col, w, mask = svv_build_versioned_csr(log.V, log.S, log.src, log.dst, log.w, log.t_add, log.t_del)
+        return self.load_csr(log.V, log.S, rp, col, w, mask)
+
+    def load_csr(self, V, S, row_ptr, col, weight, mask, inputs_on_device=False) -> LoadedGraph:
+        E = int(col.shape[0])
+        svv_load(self.h, V, E, S, row_ptr, col, weight, mask, inputs_on_device)
+        self.graph = LoadedGraph(V, S, E)
+        return self.graph
+
+    def set_tuning(self, key, value):
+        svv_set_tuning(self.h, key, value)
+
+    def stats(self) -> dict:
+        return svv_get_stats(self.h)
+
+    def device_bytes(self) -> int:
+        return svv_device_bytes(self.h)
+
+    def empty_out(self, win_len: int):
+        import torch
+        return torch.empty((win_len, self.graph.V), dtype=torch.int32, device=f"cuda:{self.device}")
+
+    def query(self, qtype, source, win_begin, win_len, out=None, stream=None, plain=False):
+        """Run one query; returns the (win_len, V) int32 tensor holding uint32 values."""
+        if out is None:
+            out = self.empty_out(win_len)
+        fn = svv_query_plain if plain else svv_query
+        fn(self.h, qtype, source, win_begin, win_len, out, stream)
+        return out
+
+    def bounds(self):
+        """(intersection values, union values, row map) of the last query, as uint32 numpy."""
+        import torch
+        V = self.graph.V
+        t = [torch.empty(V, dtype=torch.int32, device=f"cuda:{self.device}") for _ in range(3)]
+        svv_get_bounds(self.h, *t)
+        return tuple(to_u32(x) for x in t)
+
+    def query_host(self, qtype, source, win_begin, win_len, out_host, stream=None):
+        svv_query_host(self.h, qtype, source, win_begin, win_len, out_host, stream)
+        return out_host
+
+
+def to_u32(t) -> np.ndarray:
+    """Copy a result tensor to host as uint32."""
+    return t.cpu().numpy().view(np.uint32)
