@@ -166,8 +166,10 @@ def test_degenerate_graphs(svv):
 
 
 def test_isolated_source_and_no_deltas(svv):
-    log = W.random_small_log(1, V=200, n_edges=1000, S=6, n_add=0, n_del=0)
-    iso = int(np.setdiff1d(np.arange(log.V), log.src)[0])
+    log = W.random_small_log(1, V=200, n_edges=300, S=6, n_add=0, n_del=0)
+    isolated = np.setdiff1d(np.arange(log.V), log.src)
+    assert isolated.size > 0
+    iso = int(isolated[0])
     with svv.Context(0) as ctx:
         ctx.load_log(log)
         for t in TYPES:
