@@ -141,6 +141,31 @@ svv_status svv_query_host(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t
 svv_status svv_get_bounds(svv_ctx *ctx, uint32_t *cap, uint32_t *cup, uint32_t *row,
                           void *cuda_stream);
 
+/* One snapshot's full solve that allocates no memory (the paper has no
+ * counterpart: this serves callers that cannot allocate device memory when they
+ * call -- code running under an allocator that forbids cudaMalloc, plug-ins
+ * whose host owns every allocation, services that reserve all memory up front).
+ * Inputs are the caller's DEVICE arrays in the svv_load layout (row_ptr[V+1],
+ * col[E], weight[E], mask[E*ceil(S/64)]); `out` is a caller DEVICE array of V
+ * uint32 that receives the value of every vertex in snapshot `snapshot` (the
+ * same values as row snapshot-win_begin of svv_query_plain).  No context is
+ * needed: the call runs on the calling thread's current CUDA device, ordered
+ * on `cuda_stream`, and returns once the result is in `out`.
+ * Working memory is a fixed 32 MiB device array inside the library, held by
+ * every GPU that loads it until the process exits; a graph whose
+ * 4*V + 16*(V + E/64 + 64) bytes (plus 1 KiB) exceed it is rejected with
+ * SVV_EINVAL, as are bad arguments and a CSR the kernel finds malformed.  The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  No cudaMalloc,
+ * cudaFree or other allocating call is made. */
+svv_status svv_solve_snapshot_noalloc(svv_type type, uint32_t V, uint64_t E, uint32_t S,
+                                      const uint64_t *row_ptr, const uint32_t *col,
+                                      const uint32_t *weight, const uint64_t *mask,
+                                      uint32_t snapshot, uint32_t source, uint32_t *out,
+                                      void *cuda_stream);
+
 /* Tuning knobs, by name: "max_iters" (frontier-round cap per solve, 0 = V+2),
  * "spin_limit_ms" (bound on every device-side wait, default 1000),
  * "solve_chunk" / "relax_chunk" / "qrs_chunk" (edges per work unit, powers of

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libsvv.so")
 # every symbol include/svv.h declares
 EXPORTS = ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "svv_query_plain",
            "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats", "svv_device_bytes", "svv_status_str",
-           "svv_last_error", "svv_destroy")
+           "svv_last_error", "svv_destroy", "svv_solve_snapshot_noalloc")
 
 
 class SvvError(RuntimeError):
@@ -72,6 +72,8 @@ def lib():
     L.svv_last_error.restype = ctypes.c_char_p
     L.svv_destroy.argtypes = [P]
     L.svv_destroy.restype = None
+    L.svv_solve_snapshot_noalloc.argtypes = [i32, u32, u64, u32, P, P, P, P, u32, u32, P, P]
+    L.svv_solve_snapshot_noalloc.restype = i32
     for f in ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "svv_query_plain",
               "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats"):
         getattr(L, f).restype = i32
@@ -184,6 +186,13 @@ def svv_get_bounds(ctx, cap=None, cup=None, row=None, stream=None):
     _check(ctx, lib().svv_get_bounds(ctx, _ptr(cap) if cap is not None else n,
                                      _ptr(cup) if cup is not None else n,
                                      _ptr(row) if row is not None else n, _stream(stream)))
+
+
+def svv_solve_snapshot_noalloc(qtype: int, V: int, E: int, S: int, row_ptr, col, weight, mask,
+                               snapshot: int, source: int, out, stream=None):
+    """One snapshot's solve with no allocation; all arrays are device tensors."""
+    _check(None, lib().svv_solve_snapshot_noalloc(qtype, V, E, S, _ptr(row_ptr), _ptr(col), _ptr(weight),
+                                                  _ptr(mask), snapshot, source, _ptr(out), _stream(stream)))
 
 
 # --------------------------------------------------------------------------
