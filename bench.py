@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
+                   help="library tuning knob (svv_set_tuning), repeatable")
     p.add_argument("--verbose", action="store_true")
     return p.parse_args()
 
@@ -162,6 +164,31 @@ def algo_bytes(phase, gc, st, L):
     return 0
 
 
+KERNEL_SOURCES = {"cap": ["svv_solve.cu", "svv_device.cuh", "svv_push.cuh", "svv_internal.h"]}
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, only while the
+    kernel's sources still hash to the version that was captured."""
+    import hashlib
+    import re
+    if workload != "rmat20" or kernel not in KERNEL_SOURCES:
+        return None
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2502_10579_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    try:
+        with open(os.path.join(ROOT, "profiles", "solve_kernel_rmat20.md")) as fh:
+            for line in fh:
+                m = re.match(r"traffic: kernel=(\w+) bytes_per_launch=(\d+) sources_sha256=(\w+)", line.strip())
+                if m and m.group(1) == kernel and m.group(3) == h.hexdigest():
+                    return int(m.group(2))
+    except OSError:
+        pass
+    return None
+
+
 def cpu_baseline(log, qs, nthreads=0, snaps=None):
     import oracle
     cores = nthreads or os.cpu_count() or 1
@@ -260,6 +287,9 @@ def main():
     ctx = svv.Context(dev)
     ctx.load_csr(log.V, log.S, rp, col, w, mask)
     ctx.set_tuning("phase_timing", 1)
+    for kv in args.tune:
+        k, v = kv.split("=", 1)
+        ctx.set_tuning(k, int(v))
     outs = [ctx.empty_out(q.win_len) for q in qs]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=f"cuda:{dev}")
     stream = torch.cuda.current_stream(dev)
@@ -360,11 +390,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": desc, "queries_per_step": len(qs), "l2": "flushed between steps (512 MB write)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "tuning": dict(kv.split("=", 1) for kv in args.tune)},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
                          "algorithmic_bytes_per_launch": abytes / nlaunch,
-                         "avg_launch_ms": phase_ms[dom] / nlaunch, "traffic": None},
+                         "avg_launch_ms": phase_ms[dom] / nlaunch,
+                         "traffic": recorded_traffic(dom, args.workload)},
             "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
             "plain": plain, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * len(qs) * 5,

@@ -166,10 +166,26 @@ svv_status svv_solve_snapshot_noalloc(svv_type type, uint32_t V, uint64_t E, uin
                                       uint32_t snapshot, uint32_t source, uint32_t *out,
                                       void *cuda_stream);
 
+/* Per-round trace of the last svv_query (needs the "round_trace" tuning key):
+ * phase 0 = intersection solve, 1 = union solve, 2 = relaxation (last slab).
+ * out[0] = device time (ns, low 40 bits) when round 1 began after
+ * initialisation; out[r] for r >= 1 = (frontier units << 40) | start time of
+ * round r (ns, low 40 bits); entries past the last round are 0.  `out` is a
+ * HOST array of `cap` entries (at most 4096 are written); *n_out receives the
+ * number written. */
+svv_status svv_get_round_trace(svv_ctx *ctx, uint32_t phase, uint64_t *out, uint32_t cap,
+                               uint32_t *n_out);
+
 /* Tuning knobs, by name: "max_iters" (frontier-round cap per solve, 0 = V+2),
  * "spin_limit_ms" (bound on every device-side wait, default 1000),
  * "solve_chunk" / "relax_chunk" / "qrs_chunk" (edges per work unit, powers of
- * two), "blocks_per_sm" (0 = occupancy limit), "phase_timing" (1 = record
+ * two), "blocks_per_sm" (0 = occupancy limit), "delta_sssp" / "delta_sswp"
+ * (near-far width of the SSSP / SSWP solves: a frontier round relaxes only the
+ * vertices within this distance of the round's best value and keeps the rest
+ * queued; 0 relaxes every queued vertex; results are identical either way),
+ * "round_trace" (1 = record, per frontier round of the intersection solve,
+ * the union solve and the relaxation, the frontier size and a device
+ * timestamp; read with svv_get_round_trace), "phase_timing" (1 = record
  * CUDA events between the phases of each query, reported by svv_get_stats).  SVV_EINVAL on an unknown key
  * or a value out of range. */
 svv_status svv_set_tuning(svv_ctx *ctx, const char *key, int64_t value);

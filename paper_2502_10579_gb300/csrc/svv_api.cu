@@ -15,6 +15,7 @@ namespace {
 
 constexpr int kNumCtl = 8 + 256;  // 0..3 query phases, 8.. per-snapshot plain solves
 constexpr uint32_t kMaxSlab = 128;
+constexpr uint32_t kTraceCap = 4096;
 
 struct DeviceGuard {
   int prev = -1;
@@ -41,11 +42,14 @@ struct svv_ctx {
   // tuning
   uint32_t maxit = 0;
   uint32_t spin_ms = 1000;
-  uint32_t solve_cs = 6, relax_cs = 5, qrs_cs = 8;
+  uint32_t solve_cs = 5, relax_cs = 5, qrs_cs = 5;
+  uint32_t delta[3] = {0, 0, 0};  // near-far width per query type (0 = off)
   int bps = 0;
   int threads = 512;
   int occ_solve = 0, occ_qrs = 0, occ_relax = 0;
   bool phase_timing = false;
+  bool round_trace = false;
+  unsigned long long* trace = nullptr;  // [3][kTraceCap]: intersection, union, relaxation
   cudaEvent_t ev[7] = {};
 
   // resident graph
@@ -204,7 +208,7 @@ svv_status check_query(svv_ctx* c, int type, uint32_t source, uint32_t wb, uint3
   return SVV_OK;
 }
 
-SolveArgs solve_base(svv_ctx* c, uint32_t wb, uint32_t wl) {
+SolveArgs solve_base(svv_ctx* c, uint32_t wb, uint32_t wl, int type) {
   SolveArgs a{};
   a.g = c->g;
   a.win = Window{wb, wl};
@@ -214,7 +218,10 @@ SolveArgs solve_base(svv_ctx* c, uint32_t wb, uint32_t wl) {
   a.qcap = c->qcap;
   a.cshift = c->solve_cs;
   a.qerr = c->qerr;
-  a.maxit = c->maxit ? c->maxit : c->g.V + 2u;
+  a.delta = (type == 0 || type == 1) ? c->delta[type] : 0u;
+  // deferred rounds add to the round count, so the default cap is wider
+  const uint64_t cap = a.delta ? 16ull * c->g.V + 64 : (uint64_t)c->g.V + 2;
+  a.maxit = c->maxit ? c->maxit : (uint32_t)std::min<uint64_t>(cap, 0xFFFFFFF0ull);
   a.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
   return a;
 }
@@ -305,6 +312,7 @@ void svv_destroy(svv_ctx* c) {
     if (c->hqerr) cudaFreeHost(c->hqerr);
     for (auto& e : c->ev)
       if (e) cudaEventDestroy(e);
+    if (c->trace) cudaFree(c->trace);
   }
   delete c;
 }
@@ -340,6 +348,19 @@ svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
         if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
     }
     c->phase_timing = v != 0;
+  } else if (k == "round_trace") {
+    if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "round_trace is 0 or 1");
+    if (v && !c->trace) {
+      DeviceGuard dg(c->device);
+      if (cudaMalloc(&c->trace, 3 * kTraceCap * sizeof(unsigned long long)) != cudaSuccess) {
+        c->trace = nullptr;
+        return cuda_fail(c, cudaGetLastError(), "trace buffer");
+      }
+    }
+    c->round_trace = v != 0;
+  } else if (k == "delta_sssp" || k == "delta_sswp") {
+    if (v < 0 || v > 0x7FFFFFFF) return fail(c, SVV_EINVAL, k + " out of range");
+    c->delta[k == "delta_sssp" ? 0 : 1] = (uint32_t)v;
   } else if (k == "blocks_per_sm") {
     if (v < 0 || v > 4) return fail(c, SVV_EINVAL, "blocks_per_sm in [0, 4]");
     c->bps = (int)v;
@@ -532,22 +553,31 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
   if (timing) cudaEventRecord(c->ev[0], s);
 
   // a1: intersection graph (edges present in every window snapshot)
-  SolveArgs a1 = solve_base(c, wb, wl);
+  SolveArgs a1 = solve_base(c, wb, wl, t);
   a1.init = kInitSource;
   a1.source = source;
   a1.val = c->rI;
   a1.ctl = c->ctl + 0;
   a1.skip_nf = (wb == 0 && wl == c->g.S) ? 1 : 0;
+  if (c->round_trace) {
+    cudaMemsetAsync(c->trace, 0, 3 * kTraceCap * sizeof(unsigned long long), s);
+    a1.trace = c->trace;
+    a1.trace_cap = kTraceCap;
+  }
   if ((e = launch_solve(t, kPredAll, a1, cfg_for(c, c->occ_solve), s)) != cudaSuccess)
     return cuda_fail(c, e, "launch intersection solve");
   if (timing) cudaEventRecord(c->ev[1], s);
   // a2: union graph, incrementally from the intersection values
-  SolveArgs a2 = solve_base(c, wb, wl);
+  SolveArgs a2 = solve_base(c, wb, wl, t);
   a2.init = kInitSeed;
   a2.source = source;
   a2.base = c->rI;
   a2.val = c->rU;
   a2.ctl = c->ctl + 1;
+  if (c->round_trace) {
+    a2.trace = c->trace + kTraceCap;
+    a2.trace_cap = kTraceCap;
+  }
   if ((e = launch_solve(t, kPredAny, a2, cfg_for(c, c->occ_solve), s)) != cudaSuccess)
     return cuda_fail(c, e, "launch union solve");
   if (timing) cudaEventRecord(c->ev[2], s);
@@ -612,6 +642,10 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
     r.qerr = c->qerr;
     r.maxit = c->maxit ? c->maxit : c->g.V + 2u;
     r.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
+    if (c->round_trace) {
+      r.trace = c->trace + 2 * kTraceCap;
+      r.trace_cap = kTraceCap;
+    }
     if ((e = launch_relax(t, P, K, r, cfg_for(c, c->occ_relax), s)) != cudaSuccess)
       return cuda_fail(c, e, "launch relaxation");
     if (timing) cudaEventRecord(c->ev[4], s);
@@ -682,7 +716,7 @@ svv_status svv_query_plain(svv_ctx* c, svv_type type, uint32_t source, uint32_t 
     TeamCtl* slot = c->ctl + 8 + (i % (kNumCtl - 8));
     if (i >= (uint32_t)(kNumCtl - 8) && (e = cudaMemsetAsync(slot, 0, sizeof(TeamCtl), s)) != cudaSuccess)
       return cuda_fail(c, e, "memset");
-    SolveArgs a = solve_base(c, wb, wl);
+    SolveArgs a = solve_base(c, wb, wl, (int)type);
     a.init = kInitSource;
     a.source = source;
     a.bit = wb + i;
@@ -718,6 +752,18 @@ svv_status svv_get_bounds(svv_ctx* c, uint32_t* cap, uint32_t* cup, uint32_t* ro
   if (e == cudaSuccess && row) e = cudaMemcpyAsync(row, c->row, n, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "copying bounds");
+  return SVV_OK;
+}
+
+svv_status svv_get_round_trace(svv_ctx* c, uint32_t phase, uint64_t* out, uint32_t cap, uint32_t* n_out) {
+  if (!c || !out || !n_out || phase > 2) return SVV_EINVAL;
+  *n_out = 0;
+  if (!c->trace) return fail(c, SVV_EINVAL, "round_trace was never enabled");
+  DeviceGuard dg(c->device);
+  const uint32_t n = std::min(cap, kTraceCap);
+  cudaError_t e = cudaMemcpy(out, c->trace + phase * kTraceCap, n * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copying the round trace");
+  *n_out = n;
   return SVV_OK;
 }
 

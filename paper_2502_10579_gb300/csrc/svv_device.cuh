@@ -76,6 +76,51 @@ __device__ __forceinline__ bool team_sync(TeamCtl* c, uint32_t* qerr, unsigned n
 }
 
 // ---------------------------------------------------------------------------
+// One acquire load per CTA, broadcast through shared memory: a per-round
+// counter read by every thread would send one uncached request per thread to
+// the same L2 line.
+__device__ __forceinline__ void cta_read2(const unsigned* p, const unsigned* q, uint32_t& x, uint32_t& y) {
+  __shared__ uint32_t s_v[2];
+  if (threadIdx.x == 0) {
+    s_v[0] = ld_acquire(p);
+    s_v[1] = q ? ld_acquire(q) : 0u;
+  }
+  __syncthreads();
+  x = s_v[0];
+  y = s_v[1];
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t cta_read(const unsigned* p) {
+  uint32_t x, y;
+  cta_read2(p, nullptr, x, y);
+  return x;
+}
+
+// Work distribution over n units, `tk` units per batch: a warp's first batch
+// is static (batch gwarp), later ones come from `ticket`; no atomic at all when
+// the static batches cover the round.
+struct Batches {
+  uint32_t n, tk, nwarps, gwarp;
+  unsigned* ticket;
+  __device__ __forceinline__ uint32_t first() const { return gwarp * tk; }
+  __device__ __forceinline__ uint32_t next(unsigned lane) const {
+    const unsigned long long stat = (unsigned long long)nwarps * tk;
+    if (stat >= n) return n;
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(ticket, tk);
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    const unsigned long long r = stat + t;
+    return r >= n ? n : (uint32_t)r;
+  }
+};
+
+__device__ __forceinline__ uint32_t batch_size(uint32_t n, uint32_t nwarps, uint32_t cap) {
+  const uint32_t t = (n + nwarps - 1) / nwarps;
+  return t < 1u ? 1u : (t > cap ? cap : t);
+}
+
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, unsigned lane) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {

@@ -30,7 +30,7 @@ struct alignas(128) TeamCtl {
   unsigned int pad3[29];
   unsigned int err;        // kErr* of this team
   unsigned int iters;      // rounds completed
-  unsigned int aux[14];    // phase outputs (counts), see the kernels
+  unsigned int aux[14];    // phase outputs (counts) / per-round best-value ring, see the kernels
   unsigned long long relaxed;  // edges examined (diagnostic)
   unsigned long long pad4[8];
 };
@@ -75,6 +75,10 @@ struct SolveArgs {
   uint32_t* qerr;    // query-wide error word
   uint32_t maxit;
   unsigned long long spin_ns;
+  uint32_t delta;    // near-far width: a round relaxes only units within delta
+                     // of the frontier's best value (0 = relax every unit)
+  unsigned long long* trace;  // optional: per round {frontier units, start ns}
+  uint32_t trace_cap;
 };
 
 struct QrsArgs {
@@ -124,6 +128,8 @@ struct RelaxArgs {
   uint32_t* qerr;
   uint32_t maxit;
   unsigned long long spin_ns;
+  unsigned long long* trace;
+  uint32_t trace_cap;
 };
 
 struct ScatterArgs {

@@ -93,14 +93,14 @@ __device__ void qrs_walk(const QrsArgs& a, uint32_t NU, unsigned* ticket) {
   const DevGraph& g = a.g;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt = (1u << lane) - 1u;
-  for (;;) {
-    uint32_t t0 = 0;
-    if (lane == 0) t0 = atomicAdd(ticket, 32u);
-    t0 = __shfl_sync(kFullMask, t0, 0);
-    if (t0 >= NU) break;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const Batches bt{NU, batch_size(NU, nwarps, 32u), nwarps, gwarp, ticket};
+  const uint32_t tk = bt.tk;
+  for (uint32_t t0 = bt.first(); t0 < NU; t0 = bt.next(lane)) {
     const uint32_t ui = t0 + lane;
     uint32_t r = 0, beg = 0, cnt = 0, fe = 0, nfb = 0;
-    if (ui < NU) {
+    if (lane < tk && ui < NU) {
       const unsigned long long u = ld_cg(a.units + ui);
       r = (uint32_t)u;
       const uint32_t ch = (uint32_t)(u >> 32);
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kQrsThreads) qrs_kernel(QrsArgs a) {
   const DevGraph& g = a.g;
   TeamCtl* c = a.ctl;
   const unsigned nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
-  if (ld_acquire(a.qerr) != 0u) return;
+  if (cta_read(a.qerr) != 0u) return;
   const uint32_t V = g.V;
   const uint32_t C = 1u << a.cshift;
 

@@ -34,7 +34,9 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_kernel(RelaxArgs a) {
   const unsigned nthreads = gridDim.x * blockDim.x;
   const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned gwarp = gtid >> 5, nwarps = nthreads >> 5;
-  if (ld_acquire(a.qerr) != 0u) return;
+  if (cta_read(a.qerr) != 0u) return;
+  __shared__ unsigned long long s_stage[kRelaxThreads / 32][kStageUnits];
+  PushStage st{s_stage[threadIdx.x >> 5], 0u};
   const uint32_t U = a.counts[0];
   const uint32_t LP = a.LP;
   const uint32_t lps = __ffs(LP) - 1;  // LP is a power of two
@@ -46,6 +48,7 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_kernel(RelaxArgs a) {
     a.val[idx] = a.rI[a.uv[(uint32_t)(idx >> lps)]];
   for (uint32_t r = gtid; r < U; r += nthreads) a.stamp[r] = 0u;
   if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
+  if (a.trace && gtid == 0 && a.trace_cap) a.trace[0] = global_ns() & 0xFFFFFFFFFFull;
 
   // ---- round 0b: seed from addition edges with an unstable sink
   for (uint32_t k0 = gwarp * 32u; k0 < g.NF; k0 += nwarps * 32u) {
@@ -85,9 +88,10 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_kernel(RelaxArgs a) {
         const uint4 d = a.qrow[rx];
         deg = d.w - d.x;
       }
-      warp_push_units(push, rx, deg, a.cshift, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
+      stage_push_units(push, rx, deg, a.cshift, st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
     }
   }
+  stage_flush_cta(st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
   if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
 
   // ---- rounds >= 1: Algorithm 2 while-loop over the frontier
@@ -98,7 +102,8 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_kernel(RelaxArgs a) {
   uint32_t it = 1;
   for (;; ++it) {
     const uint32_t cur = it % 3u, nxt = (it + 1u) % 3u, clr = (it + 2u) % 3u;
-    uint32_t n = ld_acquire(&c->qn[cur]);
+    uint32_t n = cta_read(&c->qn[cur]);
+    if (a.trace && gtid == 0 && it < a.trace_cap) a.trace[it] = ((unsigned long long)n << 40) | (global_ns() & 0xFFFFFFFFFFull);
     if (n == 0u) break;
     if (it > a.maxit) {
       if (gtid == 0) set_err(c, a.qerr, kErrTimeout);
@@ -114,11 +119,9 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_kernel(RelaxArgs a) {
     unsigned* qn_out = &c->qn[nxt];
     const uint32_t stamp_next = it + 1u;
 
-    for (;;) {
-      uint32_t t0 = 0;
-      if (lane == 0) t0 = atomicAdd(&c->ticket[cur], (unsigned)G);
-      t0 = __shfl_sync(kFullMask, t0, 0);
-      if (t0 >= n) break;
+    // G units (one per lane group) per batch
+    const Batches bt{n, (uint32_t)G, nwarps, gwarp, &c->ticket[cur]};
+    for (uint32_t t0 = bt.first(); t0 < n; t0 = bt.next(lane)) {
       const uint32_t ui = t0 + grp;
       uint32_t beg = 0, end = 0, fe = 0, nfb = 0;
       uint32_t sv[K];
@@ -156,33 +159,57 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_kernel(RelaxArgs a) {
         bool pend = false;
         uint32_t pend_x = 0;
         const uint32_t nj = min((uint32_t)P, maxcnt - j0);
-        for (uint32_t jj = 0; jj < nj; ++jj) {
-          const uint32_t ex = __shfl_sync(kFullMask, xr, jj, P);
-          const uint32_t ew = __shfl_sync(kFullMask, w, jj, P);
-          const uint64_t em0 = __shfl_sync(kFullMask, m0, jj, P);
-          uint64_t em1 = ~0ull;
-          if (P * K > 64) em1 = __shfl_sync(kFullMask, m1, jj, P);
-          const bool ev = (beg + j0 + jj) < end;
-          bool imp = false;
-          if (ev) {
-            uint32_t* row = a.val + ((size_t)ex << lps) + gl;
+        // two edges per iteration: both target rows are loaded before either
+        // is compared, so each lane keeps two load chains in flight
+        for (uint32_t jj = 0; jj < nj; jj += 2u) {
+          uint32_t ex[2], ewt[2];
+          uint64_t em0[2], em1[2];
+          bool ev[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t src = min(jj + h, (uint32_t)P - 1u);
+            ex[h] = __shfl_sync(kFullMask, xr, src, P);
+            ewt[h] = __shfl_sync(kFullMask, w, src, P);
+            em0[h] = __shfl_sync(kFullMask, m0, src, P);
+            em1[h] = ~0ull;
+            if (P * K > 64) em1[h] = __shfl_sync(kFullMask, m1, src, P);
+            ev[h] = (jj + h < nj) && (beg + j0 + jj + h) < end;
+          }
+          uint32_t curv[2][K];
+          bool want[2][K];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t* row = a.val + ((size_t)ex[h] << lps) + gl;
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) {
               const uint32_t i = gl + kk * P;
-              const bool bit = (i < 64u) ? ((em0 >> i) & 1ull) : ((em1 >> (i - 64u)) & 1ull);
-              if (i < a.ls && bit) {
-                const uint32_t cand = Op::relax(sv[kk], ew);
-                if (Op::better(cand, ld_cg(row + kk * P))) {
+              const bool bit = (i < 64u) ? ((em0[h] >> i) & 1ull) : ((em1[h] >> (i - 64u)) & 1ull);
+              want[h][kk] = ev[h] && i < a.ls && bit;
+              curv[h][kk] = want[h][kk] ? ld_cg(row + kk * P) : 0u;
+            }
+          }
+          bool imp[2] = {false, false};
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t* row = a.val + ((size_t)ex[h] << lps) + gl;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+              if (want[h][kk]) {
+                const uint32_t cand = Op::relax(sv[kk], ewt[h]);
+                if (Op::better(cand, curv[h][kk])) {
                   const uint32_t old = Op::atomic(row + kk * P, cand);
-                  imp |= Op::better(cand, old);
+                  imp[h] |= Op::better(cand, old);
                 }
               }
             }
           }
-          const unsigned bi = __ballot_sync(kFullMask, imp) & gmask;
-          if (gl == jj && bi) {
-            pend = true;
-            pend_x = ex;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const unsigned bi = __ballot_sync(kFullMask, imp[h]) & gmask;
+            if (gl == jj + h && bi) {
+              pend = true;
+              pend_x = ex[h];
+            }
           }
         }
         bool push = false;
@@ -192,9 +219,10 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_kernel(RelaxArgs a) {
           const uint4 d = a.qrow[pend_x];
           deg = d.w - d.x;
         }
-        warp_push_units(push, pend_x, deg, a.cshift, qout, qn_out, a.qcap, c, a.qerr, lane);
+        stage_push_units(push, pend_x, deg, a.cshift, st, qout, qn_out, a.qcap, c, a.qerr, lane);
       }
     }
+    stage_flush_cta(st, qout, qn_out, a.qcap, c, a.qerr, lane);
     if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
   }
   if (gl == 0 && relaxed) atomicAdd(&c->relaxed, relaxed);

@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(_HERE, "libsvv.so")
 # every symbol include/svv.h declares
 EXPORTS = ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "svv_query_plain",
            "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats", "svv_device_bytes", "svv_status_str",
-           "svv_last_error", "svv_destroy", "svv_solve_snapshot_noalloc")
+           "svv_last_error", "svv_destroy", "svv_solve_snapshot_noalloc",
+           "svv_get_round_trace")
 
 
 class SvvError(RuntimeError):
@@ -74,6 +75,8 @@ def lib():
     L.svv_destroy.restype = None
     L.svv_solve_snapshot_noalloc.argtypes = [i32, u32, u64, u32, P, P, P, P, u32, u32, P, P]
     L.svv_solve_snapshot_noalloc.restype = i32
+    L.svv_get_round_trace.argtypes = [P, u32, P, u32, ctypes.POINTER(u32)]
+    L.svv_get_round_trace.restype = i32
     for f in ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "svv_query_plain",
               "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats"):
         getattr(L, f).restype = i32
@@ -179,6 +182,20 @@ def svv_query_plain(ctx, qtype: int, source: int, win_begin: int, win_len: int, 
 def svv_query_host(ctx, qtype: int, source: int, win_begin: int, win_len: int, out_host, stream=None):
     _check(ctx, lib().svv_query_host(ctx, qtype, source, win_begin, win_len, _ptr(out_host),
                                      _stream(stream)))
+
+
+def svv_get_round_trace(ctx, phase: int):
+    """[(frontier_units, start_ns)] per round of the last query's phase
+    (0 intersection, 1 union, 2 relaxation); round 0 holds (0, init_end_ns)."""
+    buf = np.zeros(4096, np.uint64)
+    n = ctypes.c_uint32()
+    _check(ctx, lib().svv_get_round_trace(ctx, phase, _ptr(buf), 4096, ctypes.byref(n)))
+    out = []
+    for i, x in enumerate(buf[:n.value].tolist()):
+        if x == 0 and i > 0:
+            break
+        out.append((x >> 40, x & ((1 << 40) - 1)))
+    return out
 
 
 def svv_get_bounds(ctx, cap=None, cup=None, row=None, stream=None):
