@@ -60,6 +60,15 @@ typedef enum {
     SVV_EINTERNAL = 7    /* internal capacity check failed (a library bug) */
 } svv_status;
 
+/* One instance of a batched query: the arguments of svv_query plus the status
+ * the batch call writes back. */
+typedef struct {
+    svv_type type;
+    uint32_t source, win_begin, win_len;
+    uint32_t *out;          /* caller-owned DEVICE buffer of win_len*V uint32 */
+    svv_status status;      /* written by svv_query_batch */
+} svv_query_spec;
+
 /* Per-query diagnostics of the last svv_query / svv_query_plain call. */
 typedef struct {
     uint32_t unstable;        /* U: vertices whose bounds differ (Section 3, Step 2) */
@@ -76,7 +85,9 @@ typedef struct {
      * compaction + subgraph extraction, multi-snapshot relaxation, scatter;
      * for svv_query_plain, ms_cap holds the total of the per-snapshot solves */
     float ms_cap, ms_cup, ms_qrs, ms_relax, ms_scatter;
-    float reserved;
+    float ms_batch;           /* device span of the last svv_query_batch (first start to last end) */
+    uint32_t batch_teams;     /* teams the last batch ran with */
+    uint32_t batch_team_blocks;
 } svv_stats;
 
 /* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the bytes
@@ -120,6 +131,21 @@ svv_status svv_load(svv_ctx *ctx, uint32_t V, uint64_t E, uint32_t S, const uint
  * SVV_EINVAL on type, source >= V, win_len == 0 or win_begin+win_len > S. */
 svv_status svv_query(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
                      uint32_t win_len, uint32_t *out, void *cuda_stream);
+
+/* Many queries in ONE persistent launch (the instances may mix types, sources
+ * and window lengths).  The cooperative grid is split into teams of CTAs;
+ * each team takes instances from a device work queue and runs the whole
+ * intersection-union pipeline of svv_query for each, with its own scratch, so
+ * instances overlap on the GPU.  Each spec is checked as in svv_query; an
+ * invalid spec gets SVV_EINVAL and is skipped.  Every valid spec's `out` is
+ * written as svv_query would write it, and its status is set (SVV_OK, or
+ * SVV_ETIMEOUT for an instance that hit a bounded wait or was not reached
+ * because its team stopped).  The call returns after the stream reaches the
+ * end of the batch, with SVV_OK if every spec succeeded, else the first
+ * failing status.  The number of teams ("batch_teams" tuning key, default 8)
+ * is reduced when their scratch would exceed the HBM budget; SVV_ENOMEM if not
+ * even one team fits. */
+svv_status svv_query_batch(svv_ctx *ctx, uint32_t n, svv_query_spec *specs, void *cuda_stream);
 
 /* The same query answered the plain way (Fig. 2a): one full solve per window
  * snapshot, each written straight into its row of `out`.  Same arguments and
@@ -183,7 +209,7 @@ svv_status svv_get_round_trace(svv_ctx *ctx, uint32_t phase, uint64_t *out, uint
  * (near-far width of the SSSP / SSWP solves: a frontier round relaxes only the
  * vertices within this distance of the round's best value and keeps the rest
  * queued; 0 relaxes every queued vertex; results are identical either way),
- * "round_trace" (1 = record, per frontier round of the intersection solve,
+ * "batch_teams" (teams of svv_query_batch, 1..64, default 8), "round_trace" (1 = record, per frontier round of the intersection solve,
  * the union solve and the relaxation, the frontier size and a device
  * timestamp; read with svv_get_round_trace), "phase_timing" (1 = record
  * CUDA events between the phases of each query, reported by svv_get_stats).  SVV_EINVAL on an unknown key

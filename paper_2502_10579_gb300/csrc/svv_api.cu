@@ -6,115 +6,11 @@
 #include <string>
 #include <vector>
 
-#include "../../include/svv.h"
-#include "svv_internal.h"
+#include "svv_ctx.h"
 
 using namespace svv;
 
 namespace {
-
-constexpr int kNumCtl = 8 + 256;  // 0..3 query phases, 8.. per-snapshot plain solves
-constexpr uint32_t kMaxSlab = 128;
-constexpr uint32_t kTraceCap = 4096;
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-}  // namespace
-
-struct svv_ctx {
-  int device = 0;
-  uint64_t budget = 0;      // 0 until a graph is loaded if the caller passed 0
-  bool budget_auto = false;
-  uint64_t allocated = 0;
-  int num_sms = 0;
-  std::string err;
-
-  // tuning
-  uint32_t maxit = 0;
-  uint32_t spin_ms = 1000;
-  uint32_t solve_cs = 5, relax_cs = 5, qrs_cs = 5;
-  uint32_t delta[3] = {0, 0, 0};  // near-far width per query type (0 = off)
-  int bps = 0;
-  int threads = 512;
-  int occ_solve = 0, occ_qrs = 0, occ_relax = 0;
-  bool phase_timing = false;
-  bool round_trace = false;
-  unsigned long long* trace = nullptr;  // [3][kTraceCap]: intersection, union, relaxation
-  cudaEvent_t ev[7] = {};
-
-  // resident graph
-  bool loaded = false;
-  DevGraph g{};
-  std::vector<void*> graph_bufs;
-
-  // query scratch (sized at load from V and E; the L-dependent part on demand)
-  std::vector<void*> scratch_bufs;
-  uint32_t *rI = nullptr, *rU = nullptr, *stamp = nullptr, *row = nullptr, *uv = nullptr;
-  uint32_t *part = nullptr, *qcnt = nullptr, *cur = nullptr, *qerr = nullptr;
-  uint4* qrow = nullptr;
-  uint2* qcw = nullptr;
-  unsigned long long *q0 = nullptr, *q1 = nullptr, *units = nullptr;
-  uint32_t qcap = 0, ucap = 0, ecap = 0;
-  TeamCtl* ctl = nullptr;
-  TeamCtl* hctl = nullptr;  // pinned mirror
-  uint32_t* hqerr = nullptr;
-  // window-dependent
-  uint64_t* qmask = nullptr;
-  uint64_t mcap = 0;
-  uint32_t* val = nullptr;
-  uint64_t valcap = 0;
-  uint32_t* staging = nullptr;  // device output for svv_query_host
-  uint64_t staging_cap = 0;
-
-  svv_stats stats{};
-};
-
-namespace {
-
-svv_status fail(svv_ctx* c, svv_status s, const std::string& msg) {
-  if (c) c->err = msg;
-  return s;
-}
-
-svv_status cuda_fail(svv_ctx* c, cudaError_t e, const char* what) {
-  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
-  cudaGetLastError();  // clear a sticky launch error where possible
-  return fail(c, e == cudaErrorMemoryAllocation ? SVV_ENOMEM : SVV_ECUDA, m);
-}
-
-svv_status dev_alloc(svv_ctx* c, std::vector<void*>& owner, size_t bytes, void** out) {
-  *out = nullptr;
-  if (bytes == 0) bytes = 16;
-  bytes = (bytes + 255) & ~size_t(255);
-  if (c->budget && c->allocated + bytes > c->budget)
-    return fail(c, SVV_ENOMEM,
-                "device budget exceeded: need " + std::to_string(c->allocated + bytes) + " of " +
-                    std::to_string(c->budget) + " bytes");
-  cudaError_t e = cudaMalloc(out, bytes);
-  if (e != cudaSuccess) {
-    *out = nullptr;
-    cudaGetLastError();
-    return fail(c, SVV_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-  }
-  owner.push_back(*out);
-  c->allocated += bytes;
-  return SVV_OK;
-}
-
-template <class T>
-svv_status alloc_n(svv_ctx* c, std::vector<void*>& owner, uint64_t n, T** out) {
-  return dev_alloc(c, owner, (size_t)n * sizeof(T), reinterpret_cast<void**>(out));
-}
 
 void free_list(svv_ctx* c, std::vector<void*>& bufs) {
   for (void* p : bufs) cudaFree(p);
@@ -122,6 +18,7 @@ void free_list(svv_ctx* c, std::vector<void*>& bufs) {
 }
 
 void free_graph(svv_ctx* c) {
+  free_batch(c);
   free_list(c, c->graph_bufs);
   free_list(c, c->scratch_bufs);
   c->allocated = 0;
@@ -133,33 +30,11 @@ void free_graph(svv_ctx* c) {
   c->mcap = c->valcap = c->staging_cap = 0;
 }
 
-uint32_t ceil_div(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
-
 LaunchCfg cfg_for(const svv_ctx* c, int occ) {
   int per_sm = occ;
   if (c->bps > 0) per_sm = std::min(per_sm, c->bps);
   per_sm = std::max(1, std::min(per_sm, 4));
   return LaunchCfg{c->num_sms * per_sm, c->threads};
-}
-
-// slab shape for the relaxation: P lanes per edge, K snapshots per lane
-void slab_shape(uint32_t ls, uint32_t& P, uint32_t& K) {
-  if (ls <= 8) {
-    P = 8;
-    K = 1;
-  } else if (ls <= 16) {
-    P = 16;
-    K = 1;
-  } else if (ls <= 32) {
-    P = 32;
-    K = 1;
-  } else if (ls <= 64) {
-    P = 32;
-    K = 2;
-  } else {
-    P = 32;
-    K = 4;
-  }
 }
 
 svv_status ensure_window(svv_ctx* c, uint32_t L) {
@@ -286,7 +161,8 @@ svv_status svv_create(svv_ctx** out, int device, uint64_t budget) {
   c->occ_solve = occupancy_solve(c->threads);
   c->occ_qrs = occupancy_qrs(c->threads);
   c->occ_relax = occupancy_relax(c->threads);
-  if (c->occ_solve <= 0 || c->occ_qrs <= 0 || c->occ_relax <= 0) {
+  c->occ_batch = occupancy_batch(c->threads);
+  if (c->occ_solve <= 0 || c->occ_qrs <= 0 || c->occ_relax <= 0 || c->occ_batch <= 0) {
     delete c;
     return SVV_ECUDA;
   }
@@ -348,6 +224,9 @@ svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
         if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
     }
     c->phase_timing = v != 0;
+  } else if (k == "batch_teams") {
+    if (v < 1 || v > 64) return fail(c, SVV_EINVAL, "batch_teams in [1, 64]");
+    c->batch_teams = (int)v;
   } else if (k == "round_trace") {
     if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "round_trace is 0 or 1");
     if (v && !c->trace) {

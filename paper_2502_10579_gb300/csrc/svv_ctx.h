@@ -1,0 +1,166 @@
+// svv_ctx.h -- the library context and its host-side helpers (shared by the
+// host translation units).
+#pragma once
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/svv.h"
+#include "svv_internal.h"
+
+namespace svv {
+
+constexpr int kNumCtl = 8 + 256;  // 0..3 query phases, 8.. per-snapshot plain solves
+constexpr uint32_t kMaxSlab = 128;
+constexpr uint32_t kTraceCap = 4096;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// scratch of the batch kernel's teams, sized for a window length
+struct BatchPool {
+  int teams = 0;
+  uint32_t team_blocks = 0;
+  uint32_t LP = 0, QW = 0;
+  TeamScratch* d_sc = nullptr;
+  TeamCtl* d_ctl = nullptr;
+  std::vector<void*> bufs;
+  uint64_t bytes = 0;
+  // per-instance arrays
+  uint32_t icap = 0;
+  BatchInstance* d_inst = nullptr;
+  uint32_t *d_qerr = nullptr, *d_done = nullptr;
+  unsigned long long *d_t0 = nullptr, *d_t1 = nullptr;
+  unsigned* d_next = nullptr;
+  std::vector<void*> ibufs;
+  uint64_t ibytes = 0;
+};
+
+}  // namespace svv
+
+struct svv_ctx {
+  int device = 0;
+  uint64_t budget = 0;      // 0 until a graph is loaded if the caller passed 0
+  bool budget_auto = false;
+  uint64_t allocated = 0;
+  int num_sms = 0;
+  std::string err;
+
+  // tuning
+  uint32_t maxit = 0;
+  uint32_t spin_ms = 1000;
+  uint32_t solve_cs = 5, relax_cs = 5, qrs_cs = 5;
+  uint32_t delta[3] = {0, 0, 0};  // near-far width per query type (0 = off)
+  int bps = 0;
+  int threads = 512;
+  int occ_solve = 0, occ_qrs = 0, occ_relax = 0;
+  bool phase_timing = false;
+  bool round_trace = false;
+  unsigned long long* trace = nullptr;  // [3][kTraceCap]: intersection, union, relaxation
+  cudaEvent_t ev[7] = {};
+
+  // resident graph
+  bool loaded = false;
+  svv::DevGraph g{};
+  std::vector<void*> graph_bufs;
+
+  // query scratch (sized at load from V and E; the L-dependent part on demand)
+  std::vector<void*> scratch_bufs;
+  uint32_t *rI = nullptr, *rU = nullptr, *stamp = nullptr, *row = nullptr, *uv = nullptr;
+  uint32_t *part = nullptr, *qcnt = nullptr, *cur = nullptr, *qerr = nullptr;
+  uint4* qrow = nullptr;
+  uint2* qcw = nullptr;
+  unsigned long long *q0 = nullptr, *q1 = nullptr, *units = nullptr;
+  uint32_t qcap = 0, ucap = 0, ecap = 0;
+  svv::TeamCtl* ctl = nullptr;
+  svv::TeamCtl* hctl = nullptr;  // pinned mirror
+  uint32_t* hqerr = nullptr;
+  // window-dependent
+  uint64_t* qmask = nullptr;
+  uint64_t mcap = 0;
+  uint32_t* val = nullptr;
+  uint64_t valcap = 0;
+  uint32_t* staging = nullptr;  // device output for svv_query_host
+  uint64_t staging_cap = 0;
+
+  // batched queries
+  svv::BatchPool batch;
+  int batch_teams = 8;
+  int occ_batch = 0;
+
+  svv_stats stats{};
+};
+
+namespace svv {
+
+inline svv_status fail(svv_ctx* c, svv_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+inline svv_status cuda_fail(svv_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // clear a launch error where possible
+  return fail(c, e == cudaErrorMemoryAllocation ? SVV_ENOMEM : SVV_ECUDA, m);
+}
+
+inline uint64_t round256(uint64_t b) { return (b + 255) & ~uint64_t(255); }
+
+inline svv_status dev_alloc(svv_ctx* c, std::vector<void*>& owner, size_t bytes, void** out) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = round256(bytes);
+  if (c->budget && c->allocated + bytes > c->budget)
+    return fail(c, SVV_ENOMEM,
+                "device budget exceeded: need " + std::to_string(c->allocated + bytes) + " of " +
+                    std::to_string(c->budget) + " bytes");
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    cudaGetLastError();
+    return fail(c, SVV_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  owner.push_back(*out);
+  c->allocated += bytes;
+  return SVV_OK;
+}
+
+template <class T>
+svv_status alloc_n(svv_ctx* c, std::vector<void*>& owner, uint64_t n, T** out) {
+  return dev_alloc(c, owner, (size_t)n * sizeof(T), reinterpret_cast<void**>(out));
+}
+
+inline uint32_t ceil_div(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+inline void slab_shape(uint32_t ls, uint32_t& P, uint32_t& K) {
+  if (ls <= 8) {
+    P = 8;
+    K = 1;
+  } else if (ls <= 16) {
+    P = 16;
+    K = 1;
+  } else if (ls <= 32) {
+    P = 32;
+    K = 1;
+  } else if (ls <= 64) {
+    P = 32;
+    K = 2;
+  } else {
+    P = 32;
+    K = 4;
+  }
+}
+
+void free_batch(svv_ctx* c);
+
+}  // namespace svv

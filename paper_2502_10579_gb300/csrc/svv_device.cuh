@@ -54,7 +54,7 @@ __device__ __forceinline__ bool team_sync(TeamCtl* c, uint32_t* qerr, unsigned n
       unsigned long long t0 = global_ns();
       unsigned ns = 32;
       while (ld_acquire(&c->bar_gen) == gen) {
-        if (ld_acquire(&c->err) != 0u) {
+        if (ld_acquire(&c->err) != 0u || (qerr && ld_acquire(qerr) != 0u)) {
           ok = 0;
           break;
         }
@@ -68,7 +68,7 @@ __device__ __forceinline__ bool team_sync(TeamCtl* c, uint32_t* qerr, unsigned n
       }
     }
     __threadfence();
-    if (ok && ld_acquire(&c->err) != 0u) ok = 0;
+    if (ok && (ld_acquire(&c->err) != 0u || (qerr && ld_acquire(qerr) != 0u))) ok = 0;
     s_ok = ok;
   }
   __syncthreads();

@@ -143,11 +143,62 @@ struct ScatterArgs {
   const uint32_t* qerr;
 };
 
+// ---------------------------------------------------------------------------
+// Batched queries: many (type, source, window) instances in one persistent
+// launch whose grid is split into teams.
+
+struct BatchInstance {
+  int type;
+  uint32_t source, wb, wl;
+  uint32_t* out;  // device, wl * V
+};
+
+// per-team query scratch (same roles as the single-query scratch)
+struct TeamScratch {
+  uint32_t *rI, *rU, *stamp, *row, *uv, *part, *qcnt, *cur;
+  uint4* qrow;
+  uint2* qcw;
+  uint64_t* qmask;
+  uint32_t* val;
+  unsigned long long *q0, *q1, *units;
+  uint32_t qcap, ucap, ecap;
+  unsigned long long mcap;
+};
+
+constexpr int kBatchCtl = 5;  // per team: barrier, intersection, union, extraction, relaxation
+
+struct BatchArgs {
+  DevGraph g;
+  const BatchInstance* inst;
+  uint32_t n_inst;
+  // serving: the host appends instances and raises *live_tail; the kernel
+  // waits (bounded) for more work and leaves after idle_ns without any, or
+  // when *live_stop is set.  NULL in one-shot batches.
+  const volatile uint32_t* live_tail;
+  const volatile uint32_t* live_stop;
+  unsigned long long idle_ns;
+  unsigned* next;                   // instance ticket
+  uint32_t* qerr;                   // [capacity] per-instance error words
+  volatile uint32_t* done;          // [capacity] 1 when an instance completed (any status)
+  unsigned long long* t_start;      // [capacity] device ns
+  unsigned long long* t_end;
+  const TeamScratch* scratch;       // [teams]
+  TeamCtl* ctl;                     // [teams * kBatchCtl]
+  uint32_t team_blocks;
+  uint32_t solve_cs, relax_cs, qrs_cs;
+  uint32_t delta[2];
+  uint32_t maxit;                   // 0 = per-instance default
+  unsigned long long spin_ns;
+};
+
 // launch helpers (defined in the .cu files)
 struct LaunchCfg {
   int blocks;     // cooperative grid size
   int threads;
 };
+
+cudaError_t launch_batch(const BatchArgs& b, LaunchCfg cfg, cudaStream_t s);
+int occupancy_batch(int threads);
 
 cudaError_t launch_solve(int type, int pred, const SolveArgs& a, LaunchCfg cfg, cudaStream_t s);
 cudaError_t launch_qrs(const QrsArgs& a, LaunchCfg cfg, cudaStream_t s);

@@ -19,8 +19,7 @@
 // intersection graph, whose values are already a fixed point on it, so it is
 // skipped.  Sources of seed edges hold their intersection-graph value in every
 // snapshot at that point.
-#include "svv_device.cuh"
-#include "svv_push.cuh"
+#include "svv_relax.cuh"
 
 namespace svv {
 
@@ -28,205 +27,9 @@ constexpr int kRelaxThreads = 512;
 
 template <class Op, int P, int K>
 __global__ void __launch_bounds__(kRelaxThreads) relax_kernel(RelaxArgs a) {
-  const DevGraph& g = a.g;
-  TeamCtl* c = a.ctl;
-  const unsigned lane = threadIdx.x & 31u;
-  const unsigned nthreads = gridDim.x * blockDim.x;
-  const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned gwarp = gtid >> 5, nwarps = nthreads >> 5;
-  if (cta_read(a.qerr) != 0u) return;
-  __shared__ unsigned long long s_stage[kRelaxThreads / 32][kStageUnits];
-  PushStage st{s_stage[threadIdx.x >> 5], 0u};
-  const uint32_t U = a.counts[0];
-  const uint32_t LP = a.LP;
-  const uint32_t lps = __ffs(LP) - 1;  // LP is a power of two
-  const uint32_t snap0 = a.win.b + a.s0;  // absolute snapshot of slab column 0
-
-  // ---- round 0a: values and stamps
-  const unsigned long long nval = (unsigned long long)U << lps;
-  for (unsigned long long idx = gtid; idx < nval; idx += nthreads)
-    a.val[idx] = a.rI[a.uv[(uint32_t)(idx >> lps)]];
-  for (uint32_t r = gtid; r < U; r += nthreads) a.stamp[r] = 0u;
-  if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
-  if (a.trace && gtid == 0 && a.trace_cap) a.trace[0] = global_ns() & 0xFFFFFFFFFFull;
-
-  // ---- round 0b: seed from addition edges with an unstable sink
-  for (uint32_t k0 = gwarp * 32u; k0 < g.NF; k0 += nwarps * 32u) {
-    const uint32_t k = k0 + lane;
-    bool qual = false;
-    if (k < g.NF) {
-      const uint32_t rx = a.row[__ldg(&g.nfcw[k].x)];
-      if (rx != kNone) {
-        bool any, all;
-        window_any_all(g.nfmask + (size_t)k * g.W, a.win, any, all);
-        qual = any && !all;
-      }
-    }
-    unsigned bq = __ballot_sync(kFullMask, qual);
-    while (bq) {
-      const uint32_t kj = k0 + (__ffs(bq) - 1);
-      bq &= bq - 1u;
-      const uint2 e = __ldg(g.nfcw + kj);
-      const uint32_t rx = a.row[e.x];
-      const uint32_t cand = Op::relax(a.rI[__ldg(g.nfsrc + kj)], e.y);
-      const uint64_t* m = g.nfmask + (size_t)kj * g.W;
-      bool imp = false;
-      for (uint32_t i = lane; i < a.ls; i += 32u) {
-        if (mask_bit(m, snap0 + i)) {
-          uint32_t* p = a.val + ((size_t)rx << lps) + i;
-          if (Op::better(cand, ld_cg(p))) {
-            const uint32_t old = Op::atomic(p, cand);
-            imp |= Op::better(cand, old);
-          }
-        }
-      }
-      const bool any_imp = __any_sync(kFullMask, imp);
-      bool push = false;
-      uint32_t deg = 0;
-      if (any_imp && lane == 0 && atomicExch(a.stamp + rx, 1u) != 1u) {
-        push = true;
-        const uint4 d = a.qrow[rx];
-        deg = d.w - d.x;
-      }
-      stage_push_units(push, rx, deg, a.cshift, st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
-    }
-  }
-  stage_flush_cta(st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
-  if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
-
-  // ---- rounds >= 1: Algorithm 2 while-loop over the frontier
-  constexpr int G = 32 / P;
-  const unsigned grp = lane / P, gl = lane % P;
-  const unsigned gmask = (P == 32) ? kFullMask : (((1u << P) - 1u) << (grp * P));
-  unsigned long long relaxed = 0;
-  uint32_t it = 1;
-  for (;; ++it) {
-    const uint32_t cur = it % 3u, nxt = (it + 1u) % 3u, clr = (it + 2u) % 3u;
-    uint32_t n = cta_read(&c->qn[cur]);
-    if (a.trace && gtid == 0 && it < a.trace_cap) a.trace[it] = ((unsigned long long)n << 40) | (global_ns() & 0xFFFFFFFFFFull);
-    if (n == 0u) break;
-    if (it > a.maxit) {
-      if (gtid == 0) set_err(c, a.qerr, kErrTimeout);
-      break;
-    }
-    n = min(n, a.qcap);
-    if (gtid == 0) {
-      atomicExch(&c->qn[clr], 0u);
-      atomicExch(&c->ticket[clr], 0u);
-    }
-    const unsigned long long* qin = (it & 1u) ? a.q1 : a.q0;
-    unsigned long long* qout = (it & 1u) ? a.q0 : a.q1;
-    unsigned* qn_out = &c->qn[nxt];
-    const uint32_t stamp_next = it + 1u;
-
-    // G units (one per lane group) per batch
-    const Batches bt{n, (uint32_t)G, nwarps, gwarp, &c->ticket[cur]};
-    for (uint32_t t0 = bt.first(); t0 < n; t0 = bt.next(lane)) {
-      const uint32_t ui = t0 + grp;
-      uint32_t beg = 0, end = 0, fe = 0, nfb = 0;
-      uint32_t sv[K];
-#pragma unroll
-      for (int kk = 0; kk < K; ++kk) sv[kk] = Op::kIdentity;
-      if (ui < n) {
-        const unsigned long long u = ld_cg(qin + ui);
-        const uint32_t r = (uint32_t)u, ch = (uint32_t)(u >> 32);
-        const uint4 d = a.qrow[r];
-        beg = d.x + (ch << a.cshift);
-        end = min(d.w, beg + (1u << a.cshift));
-        fe = d.y;
-        nfb = d.z;
-        const uint32_t* src = a.val + ((size_t)r << lps) + gl;
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) sv[kk] = ld_cg(src + kk * P);
-      }
-      const uint32_t cnt = end > beg ? end - beg : 0u;
-      const uint32_t maxcnt = __reduce_max_sync(kFullMask, cnt);
-      if (gl == 0) relaxed += cnt;
-      for (uint32_t j0 = 0; j0 < maxcnt; j0 += P) {
-        const uint32_t e = beg + j0 + gl;
-        uint32_t xr = 0, w = 0;
-        uint64_t m0 = ~0ull, m1 = ~0ull;
-        if (e < end) {
-          const uint2 ew = a.qcw[e];
-          xr = ew.x;
-          w = ew.y;
-          if (e >= fe) {
-            const uint64_t* mp = a.qmask + (size_t)(nfb + (e - fe)) * a.QW;
-            m0 = mask_extract(mp, a.QW, a.s0);
-            if (P * K > 64) m1 = mask_extract(mp, a.QW, a.s0 + 64u);
-          }
-        }
-        bool pend = false;
-        uint32_t pend_x = 0;
-        const uint32_t nj = min((uint32_t)P, maxcnt - j0);
-        // two edges per iteration: both target rows are loaded before either
-        // is compared, so each lane keeps two load chains in flight
-        for (uint32_t jj = 0; jj < nj; jj += 2u) {
-          uint32_t ex[2], ewt[2];
-          uint64_t em0[2], em1[2];
-          bool ev[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint32_t src = min(jj + h, (uint32_t)P - 1u);
-            ex[h] = __shfl_sync(kFullMask, xr, src, P);
-            ewt[h] = __shfl_sync(kFullMask, w, src, P);
-            em0[h] = __shfl_sync(kFullMask, m0, src, P);
-            em1[h] = ~0ull;
-            if (P * K > 64) em1[h] = __shfl_sync(kFullMask, m1, src, P);
-            ev[h] = (jj + h < nj) && (beg + j0 + jj + h) < end;
-          }
-          uint32_t curv[2][K];
-          bool want[2][K];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t* row = a.val + ((size_t)ex[h] << lps) + gl;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
-              const uint32_t i = gl + kk * P;
-              const bool bit = (i < 64u) ? ((em0[h] >> i) & 1ull) : ((em1[h] >> (i - 64u)) & 1ull);
-              want[h][kk] = ev[h] && i < a.ls && bit;
-              curv[h][kk] = want[h][kk] ? ld_cg(row + kk * P) : 0u;
-            }
-          }
-          bool imp[2] = {false, false};
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t* row = a.val + ((size_t)ex[h] << lps) + gl;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
-              if (want[h][kk]) {
-                const uint32_t cand = Op::relax(sv[kk], ewt[h]);
-                if (Op::better(cand, curv[h][kk])) {
-                  const uint32_t old = Op::atomic(row + kk * P, cand);
-                  imp[h] |= Op::better(cand, old);
-                }
-              }
-            }
-          }
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const unsigned bi = __ballot_sync(kFullMask, imp[h]) & gmask;
-            if (gl == jj + h && bi) {
-              pend = true;
-              pend_x = ex[h];
-            }
-          }
-        }
-        bool push = false;
-        uint32_t deg = 0;
-        if (pend && atomicExch(a.stamp + pend_x, stamp_next) != stamp_next) {
-          push = true;
-          const uint4 d = a.qrow[pend_x];
-          deg = d.w - d.x;
-        }
-        stage_push_units(push, pend_x, deg, a.cshift, st, qout, qn_out, a.qcap, c, a.qerr, lane);
-      }
-    }
-    stage_flush_cta(st, qout, qn_out, a.qcap, c, a.qerr, lane);
-    if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
-  }
-  if (gl == 0 && relaxed) atomicAdd(&c->relaxed, relaxed);
-  if (gtid == 0) c->iters = it - 1u;
+  __shared__ unsigned long long s_stage[(kRelaxThreads / 32) * kStageUnits];
+  const Team t{a.ctl, a.qerr, gridDim.x, blockIdx.x, a.spin_ns};
+  relax_team<Op, P, K>(a, t, s_stage);
 }
 
 // ---------------------------------------------------------------------------

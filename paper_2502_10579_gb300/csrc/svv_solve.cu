@@ -14,238 +14,17 @@
 // the concatenated edge list two 32-edge steps at a time, so lanes stay busy
 // whatever the degree mix and each lane keeps two load chains in flight.  Relaxation is atomicMin/atomicMax; a vertex joins
 // the next frontier once per round (stamp dedupe).
-#include "svv_device.cuh"
-#include "svv_push.cuh"
+#include "svv_solve.cuh"
 
 namespace svv {
 
 constexpr int kSolveThreads = 512;
 
-// Near-far ordering key of a value: larger = closer to the source, so one
-// atomicMax per round finds the frontier's best value for both lattices.
-template <class Op>
-__device__ __forceinline__ uint32_t nf_key(uint32_t v) {
-  return Op::better(0u, 1u) ? ~v : v;
-}
-
 template <class Op, int PRED>
 __global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs a) {
-  const DevGraph& g = a.g;
-  TeamCtl* c = a.ctl;
-  const unsigned lane = threadIdx.x & 31u;
-  const unsigned nthreads = gridDim.x * blockDim.x;
-  const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned gwarp = gtid >> 5, nwarps = nthreads >> 5;
-  if (a.qerr && cta_read(a.qerr) != 0u) return;
-  __shared__ unsigned long long s_stage[kSolveThreads / 32][kStageUnits];
-  PushStage st{s_stage[threadIdx.x >> 5], 0u};
-
-  // round 0: starting values and stamps
-  if (a.init == kInitSource) {
-    for (uint32_t v = gtid; v < g.V; v += nthreads) {
-      a.val[v] = Op::kIdentity;
-      a.stamp[v] = 0u;
-    }
-  } else {
-    for (uint32_t v = gtid; v < g.V; v += nthreads) {
-      a.val[v] = a.base[v];
-      a.stamp[v] = 0u;
-    }
-  }
-  if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
-  if (a.trace && gtid == 0 && a.trace_cap) a.trace[0] = global_ns() & 0xFFFFFFFFFFull;
-
-  // round 0: first frontier (stamp 1, queue q1, count qn[1])
-  if (a.init == kInitSource) {
-    if (gwarp == 0) {
-      uint32_t deg = 0;
-      if (lane == 0) {
-        a.val[a.source] = Op::kSource;
-        a.stamp[a.source] = 1u;
-        deg = g.rp[a.source + 1] - g.rp[a.source];
-      }
-      stage_push_units(lane == 0, a.source, deg, a.cshift, st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
-      if (lane == 0) atomicMax(&c->aux[1], nf_key<Op>(Op::kSource));
-    }
-  } else {
-    // edges present in some but not all window snapshots (the window's
-    // addition batches); intersection edges cannot improve a fixed point of
-    // the intersection graph, so they are skipped
-    for (uint32_t k0 = gwarp * 32u; k0 < g.NF; k0 += nwarps * 32u) {
-      const uint32_t k = k0 + lane;
-      bool push = false;
-      uint32_t x = 0, deg = 0, cand = 0;
-      if (k < g.NF) {
-        bool any, all;
-        window_any_all(g.nfmask + (size_t)k * g.W, a.win, any, all);
-        if (any && !all) {
-          const uint32_t u = __ldg(g.nfsrc + k);
-          const uint2 e = __ldg(g.nfcw + k);
-          x = e.x;
-          cand = Op::relax(ld_cg(a.val + u), e.y);
-          if (Op::better(cand, ld_cg(a.val + x))) {
-            const uint32_t old = Op::atomic(a.val + x, cand);
-            if (Op::better(cand, old) && atomicExch(a.stamp + x, 1u) != 1u) {
-              push = true;
-              deg = g.rp[x + 1] - g.rp[x];
-            }
-          }
-        }
-      }
-      stage_push_units(push, x, deg, a.cshift, st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
-      warp_fold_max(push, nf_key<Op>(cand), &c->aux[1], lane);
-    }
-  }
-  stage_flush_cta(st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
-  if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
-
-  unsigned long long relaxed = 0;
-  uint32_t it = 1;
-  for (;; ++it) {
-    const uint32_t cur = it % 3u, nxt = (it + 1u) % 3u, clr = (it + 2u) % 3u;
-    const bool far_on = a.delta != 0u;
-    uint32_t n, slot;
-    cta_read2(&c->qn[cur], far_on ? &c->aux[cur] : nullptr, n, slot);
-    if (a.trace && gtid == 0 && it < a.trace_cap) a.trace[it] = ((unsigned long long)n << 40) | (global_ns() & 0xFFFFFFFFFFull);
-    if (n == 0u) break;
-    if (it > a.maxit) {
-      if (gtid == 0) set_err(c, a.qerr, kErrTimeout);
-      break;
-    }
-    n = min(n, a.qcap);
-    if (gtid == 0) {
-      atomicExch(&c->qn[clr], 0u);
-      atomicExch(&c->ticket[clr], 0u);
-      atomicExch(&c->aux[clr], 0u);
-    }
-    const unsigned long long* qin = (it & 1u) ? a.q1 : a.q0;
-    unsigned long long* qout = (it & 1u) ? a.q0 : a.q1;
-    unsigned* qn_out = &c->qn[nxt];
-    const uint32_t stamp_next = it + 1u;
-    // near-far: relax only units whose value is within delta of the best
-    // value queued for this round (that unit itself always qualifies, so every
-    // round makes progress); the others are queued again unchanged
-    uint32_t bound = 0;
-    if (far_on) {
-      if (Op::better(0u, 1u)) {
-        const uint32_t best = ~slot;
-        bound = best > kInf - a.delta ? kInf : best + a.delta;
-      } else {
-        bound = slot > a.delta ? slot - a.delta : 0u;
-      }
-    }
-
-    // units per ticket: spread a small frontier over every warp, batch a
-    // large one 32 units at a time
-    const Batches bt{n, batch_size(n, nwarps, 32u), nwarps, gwarp, &c->ticket[cur]};
-    const uint32_t tk = bt.tk;
-    for (uint32_t t0 = bt.first(); t0 < n; t0 = bt.next(lane)) {
-      const uint32_t ui = t0 + lane;
-      uint32_t beg = 0, cnt = 0, fe = 0, nfb = 0, sv = Op::kIdentity;
-      bool defer = false;
-      uint32_t dv = 0, ddeg = 0;
-      if (lane < tk && ui < n) {
-        const unsigned long long u = ld_cg(qin + ui);
-        const uint32_t v = (uint32_t)u, ch = (uint32_t)(u >> 32);
-        const uint32_t r0 = __ldg(g.rp + v), r1 = __ldg(g.rp + v + 1);
-        const uint32_t nf0 = __ldg(g.nfp + v), nf1 = __ldg(g.nfp + v + 1);
-        fe = r1 - (nf1 - nf0);
-        nfb = nf0;
-        beg = r0 + (ch << a.cshift);
-        uint32_t end = min(r1, beg + (1u << a.cshift));
-        if (PRED == kPredAll && a.skip_nf) end = min(end, fe);
-        cnt = end > beg ? end - beg : 0u;
-        sv = ld_cg(a.val + v);
-        if (far_on && (Op::better(0u, 1u) ? sv > bound : sv < bound)) {
-          // far: queue all of v's units again, once per round (stamp), and
-          // skip this one now
-          cnt = 0;
-          if (atomicExch(a.stamp + v, stamp_next) != stamp_next) {
-            defer = true;
-            dv = v;
-            ddeg = r1 - r0;
-          }
-        }
-      }
-      if (far_on) {
-        stage_push_units(defer, dv, ddeg, a.cshift, st, qout, qn_out, a.qcap, c, a.qerr, lane);
-        warp_fold_max(defer, nf_key<Op>(sv), &c->aux[nxt], lane);
-      }
-      const uint32_t incl = warp_incl_scan(cnt, lane);
-      const uint32_t total = __shfl_sync(kFullMask, incl, 31);
-      if (lane == 0) relaxed += total;
-      // two 32-edge steps in flight per iteration: their loads, checks and
-      // atomics are independent, so each lane keeps two chains going
-      for (uint32_t p0 = 0; p0 < total; p0 += 64u) {
-        bool push[2];
-        uint32_t x[2], deg[2];
-        uint32_t sk[2], ew_w[2];
-        bool act[2];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const uint32_t p = p0 + 32u * j + lane;
-          const int k = warp_owner(incl, p < total ? p : total - 1u);
-          const uint32_t ik = __shfl_sync(kFullMask, incl, k);
-          const uint32_t ck = __shfl_sync(kFullMask, cnt, k);
-          const uint32_t bk = __shfl_sync(kFullMask, beg, k);
-          const uint32_t fk = __shfl_sync(kFullMask, fe, k);
-          const uint32_t nk = __shfl_sync(kFullMask, nfb, k);
-          sk[j] = __shfl_sync(kFullMask, sv, k);
-          push[j] = false;
-          x[j] = 0;
-          deg[j] = 0;
-          act[j] = false;
-          ew_w[j] = 0;
-          if (p < total) {
-            const uint32_t e = bk + (p - (ik - ck));
-            const uint2 ew = __ldg(g.cw + e);
-            x[j] = ew.x;
-            ew_w[j] = ew.y;
-            bool present = true;
-            if (e >= fk) {
-              const uint64_t* m = g.nfmask + (size_t)(nk + (e - fk)) * g.W;
-              if (PRED == kPredAll) present = window_all(m, a.win);
-              else if (PRED == kPredAny) present = window_any(m, a.win);
-              else present = mask_bit(m, a.bit);
-            }
-            act[j] = present;
-          }
-        }
-        uint32_t cand[2], curv[2];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          cand[j] = Op::relax(sk[j], ew_w[j]);
-          curv[j] = act[j] ? ld_cg(a.val + x[j]) : cand[j];
-        }
-        bool imp[2];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          imp[j] = false;
-          if (act[j] && Op::better(cand[j], curv[j])) {
-            const uint32_t old = Op::atomic(a.val + x[j], cand[j]);
-            imp[j] = Op::better(cand[j], old);
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          if (imp[j] && atomicExch(a.stamp + x[j], stamp_next) != stamp_next) {
-            push[j] = true;
-            deg[j] = __ldg(g.rp + x[j] + 1) - __ldg(g.rp + x[j]);
-          }
-        }
-        stage_push_units(push[0], x[0], deg[0], a.cshift, st, qout, qn_out, a.qcap, c, a.qerr, lane);
-        stage_push_units(push[1], x[1], deg[1], a.cshift, st, qout, qn_out, a.qcap, c, a.qerr, lane);
-        if (far_on) {
-          const uint32_t k0v = push[0] ? nf_key<Op>(cand[0]) : 0u, k1v = push[1] ? nf_key<Op>(cand[1]) : 0u;
-          warp_fold_max(push[0] || push[1], max(k0v, k1v), &c->aux[nxt], lane);
-        }
-      }
-    }
-    stage_flush_cta(st, qout, qn_out, a.qcap, c, a.qerr, lane);
-    if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
-  }
-  if (lane == 0 && relaxed) atomicAdd(&c->relaxed, relaxed);
-  if (gtid == 0) c->iters = it - 1u;
+  __shared__ unsigned long long s_stage[(kSolveThreads / 32) * kStageUnits];
+  const Team t{a.ctl, a.qerr, gridDim.x, blockIdx.x, a.spin_ns};
+  solve_team<Op, PRED>(a, t, s_stage);
 }
 
 template <class Op, int PRED>

@@ -23,13 +23,18 @@ LIB_PATH = os.path.join(_HERE, "libsvv.so")
 EXPORTS = ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "svv_query_plain",
            "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats", "svv_device_bytes", "svv_status_str",
            "svv_last_error", "svv_destroy", "svv_solve_snapshot_noalloc",
-           "svv_get_round_trace")
+           "svv_get_round_trace", "svv_query_batch")
 
 
 class SvvError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class svv_query_spec(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("source", ctypes.c_uint32), ("win_begin", ctypes.c_uint32),
+                ("win_len", ctypes.c_uint32), ("out", ctypes.c_void_p), ("status", ctypes.c_int)]
 
 
 class svv_stats(ctypes.Structure):
@@ -40,7 +45,8 @@ class svv_stats(ctypes.Structure):
                 ("edges_relaxed_cap", ctypes.c_uint64), ("edges_relaxed_cup", ctypes.c_uint64),
                 ("edges_relaxed_multi", ctypes.c_uint64), ("ms_cap", ctypes.c_float),
                 ("ms_cup", ctypes.c_float), ("ms_qrs", ctypes.c_float), ("ms_relax", ctypes.c_float),
-                ("ms_scatter", ctypes.c_float), ("reserved", ctypes.c_float)]
+                ("ms_scatter", ctypes.c_float), ("ms_batch", ctypes.c_float),
+                ("batch_teams", ctypes.c_uint32), ("batch_team_blocks", ctypes.c_uint32)]
 
 
 _lib = None
@@ -77,6 +83,8 @@ def lib():
     L.svv_solve_snapshot_noalloc.restype = i32
     L.svv_get_round_trace.argtypes = [P, u32, P, u32, ctypes.POINTER(u32)]
     L.svv_get_round_trace.restype = i32
+    L.svv_query_batch.argtypes = [P, u32, ctypes.POINTER(svv_query_spec), P]
+    L.svv_query_batch.restype = i32
     for f in ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "svv_query_plain",
               "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats"):
         getattr(L, f).restype = i32
@@ -184,6 +192,23 @@ def svv_query_host(ctx, qtype: int, source: int, win_begin: int, win_len: int, o
                                      _stream(stream)))
 
 
+def svv_query_batch(ctx, specs, stream=None):
+    """specs: list of (type, source, win_begin, win_len, out_tensor).  Returns
+    the per-instance statuses; raises on a batch-level failure only when no
+    instance could run."""
+    n = len(specs)
+    arr = (svv_query_spec * max(n, 1))()
+    for i, (t, s, b, L, out) in enumerate(specs):
+        arr[i].type, arr[i].source, arr[i].win_begin, arr[i].win_len = t, s, b, L
+        arr[i].out = _ptr(out).value if out is not None else None
+        arr[i].status = -1
+    st = lib().svv_query_batch(ctx, n, arr, _stream(stream))
+    statuses = [int(arr[i].status) for i in range(n)]
+    if st != 0 and all(x != 0 for x in statuses):
+        _check(ctx, st)
+    return statuses
+
+
 def svv_get_round_trace(ctx, phase: int):
     """[(frontier_units, start_ns)] per round of the last query's phase
     (0 intersection, 1 union, 2 relaxation); round 0 holds (0, init_end_ns)."""
@@ -276,6 +301,17 @@ class Context:
         fn = svv_query_plain if plain else svv_query
         fn(self.h, qtype, source, win_begin, win_len, out, stream)
         return out
+
+    def query_batch(self, specs, stream=None):
+        """specs: list of (type, source, win_begin, win_len[, out]); returns
+        (outputs, statuses)."""
+        full = []
+        for sp in specs:
+            t, s, b, L = sp[:4]
+            out = sp[4] if len(sp) > 4 else self.empty_out(L)
+            full.append((t, s, b, L, out))
+        st = svv_query_batch(self.h, full, stream)
+        return [f[4] for f in full], st
 
     def bounds(self):
         """(intersection values, union values, row map) of the last query, as uint32 numpy."""
