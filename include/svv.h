@@ -147,6 +147,46 @@ svv_status svv_query(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_
  * even one team fits. */
 svv_status svv_query_batch(svv_ctx *ctx, uint32_t n, svv_query_spec *specs, void *cuda_stream);
 
+/* ---- Serving: requests that arrive while others run -------------------------
+ * svv_serve_start keeps the batch kernel of svv_query_batch running on a
+ * library stream as a live server: submitted requests enter a ring in
+ * host-mapped memory, an idle team starts each one as soon as it is free, and
+ * running requests overlap on the GPU.  The graph, the bitmasks and every
+ * team's bound/value state stay resident.  Requests with out == NULL get their
+ * output from a device arena of `arena_bytes` (0 = whatever the HBM budget
+ * leaves); a request that does not fit is refused with SVV_EBUSY until earlier
+ * results are released -- that is the admission control.  The kernel leaves
+ * after an idle period and is relaunched by the next svv_submit or svv_poll.
+ * max_window bounds win_len; capacity is the number of requests that may be
+ * submitted and not yet released.  SVV_ENOMEM if the team scratch or the
+ * arena does not fit the budget. */
+svv_status svv_serve_start(svv_ctx *ctx, uint32_t max_window, uint32_t capacity,
+                           uint64_t arena_bytes);
+
+/* Queue one request (spec->status is ignored).  *ticket identifies it.
+ * SVV_EBUSY when the ring or the arena is full (nothing was queued);
+ * SVV_EINVAL as svv_query for bad arguments or win_len > max_window. */
+svv_status svv_submit(svv_ctx *ctx, const svv_query_spec *spec, uint64_t *ticket);
+
+/* Completion of a request: returns SVV_OK and sets *result (the request's own
+ * status, as svv_query would return it) once it is done; with wait == 0 returns
+ * SVV_EBUSY while it is still queued or running; with wait != 0 blocks (bounded
+ * by 60 s, then SVV_ETIMEOUT).  Reads host-mapped memory: no CUDA call unless
+ * the server must be relaunched. */
+svv_status svv_poll(svv_ctx *ctx, uint64_t ticket, int wait, svv_status *result);
+
+/* The device buffer holding a request's output (its own or the arena's) and
+ * the device times (ns, %globaltimer) at which a team started and finished it.
+ * Valid until svv_release. */
+svv_status svv_ticket_info(svv_ctx *ctx, uint64_t ticket, uint32_t **out,
+                           uint64_t *device_start_ns, uint64_t *device_end_ns);
+
+/* Free a finished request's slot and arena space (SVV_EBUSY while running). */
+svv_status svv_release(svv_ctx *ctx, uint64_t ticket);
+
+/* Stop the server (pending requests are abandoned) and free its memory. */
+svv_status svv_serve_stop(svv_ctx *ctx);
+
 /* The same query answered the plain way (Fig. 2a): one full solve per window
  * snapshot, each written straight into its row of `out`.  Same arguments and
  * output as svv_query; on failure the rows of `out` are unspecified. */

@@ -18,6 +18,7 @@ void free_list(svv_ctx* c, std::vector<void*>& bufs) {
 }
 
 void free_graph(svv_ctx* c) {
+  free_serve(c);
   free_batch(c);
   free_list(c, c->graph_bufs);
   free_list(c, c->scratch_bufs);

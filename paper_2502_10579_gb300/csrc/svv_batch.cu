@@ -195,14 +195,15 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(BatchArgs b) {
   const Team base{tc, nullptr, b.team_blocks, rank, b.spin_ns};
   for (;;) {
     if (rank == 0 && threadIdx.x == 0) {
-      const uint32_t i = pick_instance(b);
-      tc->aux[0] = i;
+      const uint32_t id = pick_instance(b);
+      tc->aux[0] = id;
       for (int p = 1; p < kBatchCtl; ++p) zero_phase(tc + p);
-      if (i != kNoInst) b.t_start[i] = global_ns();
+      if (id != kNoInst) b.t_start[b.ring ? id % b.ring : id] = global_ns();
     }
     if (!base.sync()) return;
-    const uint32_t i = cta_read(&tc->aux[0]);
-    if (i == kNoInst) return;
+    const uint32_t id = cta_read(&tc->aux[0]);
+    if (id == kNoInst) return;
+    const uint32_t i = b.ring ? id % b.ring : id;  // slot of the instance
     const BatchInstance q = b.inst[i];
     Team t = base;
     t.qerr = b.qerr + i;

@@ -15,9 +15,10 @@ void free_batch(svv_ctx* c) {
 }
 
 namespace {
+}  // namespace
 
 // bytes one team needs for windows up to L (its share of query scratch)
-uint64_t team_bytes(const svv_ctx* c, uint32_t LP, uint32_t QW, uint32_t team_blocks) {
+static uint64_t team_bytes(const svv_ctx* c, uint32_t LP, uint32_t QW, uint32_t team_blocks) {
   const uint64_t V = c->g.V, E = std::max<uint32_t>(c->g.E, 1), NF = std::max<uint32_t>(c->g.NF, 1);
   const uint64_t qcap = V + E / (1u << std::min(c->solve_cs, c->relax_cs)) + 64;
   const uint64_t ucap = V + E / (1u << c->qrs_cs) + 64;
@@ -33,7 +34,7 @@ uint64_t team_bytes(const svv_ctx* c, uint32_t LP, uint32_t QW, uint32_t team_bl
   return b;
 }
 
-svv_status alloc_team(svv_ctx* c, std::vector<void*>& owner, uint32_t LP, uint32_t QW, uint32_t team_blocks,
+static svv_status alloc_team(svv_ctx* c, std::vector<void*>& owner, uint32_t LP, uint32_t QW, uint32_t team_blocks,
                       TeamScratch& t) {
   const uint64_t V = c->g.V, E = std::max<uint32_t>(c->g.E, 1), NF = std::max<uint32_t>(c->g.NF, 1);
   const uint64_t qcap = V + E / (1u << std::min(c->solve_cs, c->relax_cs)) + 64;
@@ -96,6 +97,8 @@ svv_status ensure_pool(svv_ctx* c, int want_teams, uint32_t L) {
   p.bytes = c->allocated - before;
   return SVV_OK;
 }
+
+namespace {
 
 svv_status ensure_instances(svv_ctx* c, uint32_t n) {
   BatchPool& p = c->batch;

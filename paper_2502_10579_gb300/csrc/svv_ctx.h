@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <deque>
 #include <string>
 #include <vector>
 
@@ -44,6 +45,44 @@ struct BatchPool {
   unsigned* d_next = nullptr;
   std::vector<void*> ibufs;
   uint64_t ibytes = 0;
+};
+
+// serving: instance ring in host-mapped memory, output arena, live kernel
+struct ServeSlot {
+  uint64_t ticket = 0;
+  bool busy = false;     // submitted, not yet released
+  bool arena = false;    // output lives in the arena
+  uint64_t off = 0, size = 0;
+  uint32_t* out = nullptr;
+};
+
+struct ServeState {
+  bool active = false;
+  uint32_t cap = 0, maxL = 0;
+  BatchInstance* h_inst = nullptr;
+  BatchInstance* d_inst = nullptr;
+  uint32_t *h_ctrl = nullptr, *d_ctrl = nullptr;  // [0] tail, [1] stop
+  uint32_t *h_done = nullptr, *d_done = nullptr;
+  uint32_t *h_qerr = nullptr, *d_qerr = nullptr;
+  unsigned long long *h_t0 = nullptr, *d_t0 = nullptr, *h_t1 = nullptr, *d_t1 = nullptr;
+  unsigned* d_next = nullptr;
+  uint64_t tail = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool launched = false;
+  uint64_t launches = 0;
+  // output arena: a ring of allocations released roughly in order
+  struct Alloc {
+    uint64_t off, size;
+    bool freed;
+  };
+  unsigned char* arena = nullptr;
+  uint64_t arena_bytes = 0, a_end = 0;  // a_end: end of the newest allocation
+  std::deque<Alloc> allocs;             // in allocation order
+  std::vector<ServeSlot> slots;
+  std::vector<void*> bufs;
+  uint64_t bytes = 0;
+  unsigned long long idle_ns = 200000000ull;
 };
 
 }  // namespace svv
@@ -95,6 +134,7 @@ struct svv_ctx {
 
   // batched queries
   svv::BatchPool batch;
+  svv::ServeState serve;
   int batch_teams = 8;
   int occ_batch = 0;
 
@@ -162,5 +202,10 @@ inline void slab_shape(uint32_t ls, uint32_t& P, uint32_t& K) {
 }
 
 void free_batch(svv_ctx* c);
+void free_serve(svv_ctx* c);
+BatchArgs batch_args(svv_ctx* c);
+svv_status ensure_pool(svv_ctx* c, int want_teams, uint32_t L);
+svv_status status_of(uint32_t qerr, uint32_t done);
+svv_status check_spec(const svv_ctx* c, const svv_query_spec& q);
 
 }  // namespace svv

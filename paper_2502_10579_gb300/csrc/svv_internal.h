@@ -177,6 +177,7 @@ struct BatchArgs {
   const volatile uint32_t* live_tail;
   const volatile uint32_t* live_stop;
   unsigned long long idle_ns;
+  uint32_t ring;                    // serving: instance i lives in slot i % ring (0 = no ring)
   unsigned* next;                   // instance ticket
   uint32_t* qerr;                   // [capacity] per-instance error words
   volatile uint32_t* done;          // [capacity] 1 when an instance completed (any status)

@@ -23,7 +23,8 @@ LIB_PATH = os.path.join(_HERE, "libsvv.so")
 EXPORTS = ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "svv_query_plain",
            "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats", "svv_device_bytes", "svv_status_str",
            "svv_last_error", "svv_destroy", "svv_solve_snapshot_noalloc",
-           "svv_get_round_trace", "svv_query_batch")
+           "svv_get_round_trace", "svv_query_batch", "svv_serve_start", "svv_submit", "svv_poll",
+           "svv_ticket_info", "svv_release", "svv_serve_stop")
 
 
 class SvvError(RuntimeError):
@@ -85,6 +86,14 @@ def lib():
     L.svv_get_round_trace.restype = i32
     L.svv_query_batch.argtypes = [P, u32, ctypes.POINTER(svv_query_spec), P]
     L.svv_query_batch.restype = i32
+    L.svv_serve_start.argtypes = [P, u32, u32, u64]
+    L.svv_submit.argtypes = [P, ctypes.POINTER(svv_query_spec), ctypes.POINTER(u64)]
+    L.svv_poll.argtypes = [P, u64, i32, ctypes.POINTER(i32)]
+    L.svv_ticket_info.argtypes = [P, u64, ctypes.POINTER(P), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    L.svv_release.argtypes = [P, u64]
+    L.svv_serve_stop.argtypes = [P]
+    for f in ("svv_serve_start", "svv_submit", "svv_poll", "svv_ticket_info", "svv_release", "svv_serve_stop"):
+        getattr(L, f).restype = i32
     for f in ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "svv_query_plain",
               "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats"):
         getattr(L, f).restype = i32
@@ -207,6 +216,73 @@ def svv_query_batch(ctx, specs, stream=None):
     if st != 0 and all(x != 0 for x in statuses):
         _check(ctx, st)
     return statuses
+
+
+def svv_serve_start(ctx, max_window: int, capacity: int = 4096, arena_bytes: int = 0):
+    _check(ctx, lib().svv_serve_start(ctx, max_window, capacity, arena_bytes))
+
+
+def svv_submit(ctx, qtype: int, source: int, win_begin: int, win_len: int, out=None):
+    """Queue a request; returns its ticket, or None when the server is full (SVV_EBUSY)."""
+    spec = svv_query_spec()
+    spec.type, spec.source, spec.win_begin, spec.win_len = qtype, source, win_begin, win_len
+    spec.out = _ptr(out).value if out is not None else None
+    t = ctypes.c_uint64()
+    st = lib().svv_submit(ctx, ctypes.byref(spec), ctypes.byref(t))
+    if st == 5:
+        return None
+    _check(ctx, st)
+    return int(t.value)
+
+
+def svv_poll(ctx, ticket: int, wait: bool = False):
+    """The request's status once done, else None."""
+    r = ctypes.c_int()
+    st = lib().svv_poll(ctx, ticket, 1 if wait else 0, ctypes.byref(r))
+    if st == 5:
+        return None
+    _check(ctx, st)
+    return int(r.value)
+
+
+def svv_ticket_info(ctx, ticket: int):
+    """(device output address, device start ns, device end ns)."""
+    out, t0, t1 = ctypes.c_void_p(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(ctx, lib().svv_ticket_info(ctx, ticket, ctypes.byref(out), ctypes.byref(t0), ctypes.byref(t1)))
+    return int(out.value or 0), int(t0.value), int(t1.value)
+
+
+def svv_release(ctx, ticket: int):
+    _check(ctx, lib().svv_release(ctx, ticket))
+
+
+def svv_serve_stop(ctx):
+    _check(ctx, lib().svv_serve_stop(ctx))
+
+
+_cudart = None
+
+
+def device_u32(address: int, n: int) -> np.ndarray:
+    """Copy n uint32 at a device address (e.g. a serving arena output) to host."""
+    global _cudart
+    if _cudart is None:
+        for name in ("libcudart.so", "libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so"):
+            try:
+                _cudart = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if _cudart is None:
+            raise RuntimeError("libcudart not found")
+        _cudart.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+        _cudart.cudaMemcpy.restype = ctypes.c_int
+    out = np.empty(n, np.uint32)
+    if n:
+        rc = _cudart.cudaMemcpy(out.ctypes.data, address, 4 * n, 2)  # cudaMemcpyDeviceToHost
+        if rc != 0:
+            raise RuntimeError(f"cudaMemcpy failed ({rc})")
+    return out
 
 
 def svv_get_round_trace(ctx, phase: int):

@@ -1,0 +1,91 @@
+"""Serving: requests submitted while others run must each give exactly the
+result of the same query run alone (and of the oracle), and the server must
+overlap requests on the GPU and refuse work when its output arena is full."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def svv():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_10579_gb300 import svv as mod
+    assert torch.cuda.is_available()
+    return mod
+
+
+def _requests(log, n, seed, l_hi):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        L = int(rng.integers(1, l_hi + 1))
+        out.append((int(rng.integers(0, 3)), int(rng.integers(0, log.V)), int(rng.integers(0, log.S - L + 1)), L))
+    return out
+
+
+def test_serve_mix_equals_alone(svv):
+    log = W.scaled_rmat(scale=14, edge_factor=8, n_snapshots=100, rate=0.002, seed=55, add_mode="skewed")
+    reqs = _requests(log, 48, 9, 100)
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        alone = [svv.to_u32(ctx.query(t, s, b, L)) for t, s, b, L in reqs]
+        svv.svv_serve_start(ctx.h, max_window=100, capacity=64)
+        rng = np.random.default_rng(1)
+        tickets = []
+        for r in reqs:
+            while True:
+                tk = svv.svv_submit(ctx.h, *r)
+                if tk is not None:
+                    break
+                time.sleep(0.001)  # arena full: admission waits for memory
+            tickets.append(tk)
+            time.sleep(float(rng.exponential(0.0005)))
+        spans = []
+        for tk, (t, s, b, L), want in zip(tickets, reqs, alone):
+            assert svv.svv_poll(ctx.h, tk, wait=True) == 0
+            addr, t0, t1 = svv.svv_ticket_info(ctx.h, tk)
+            got = svv.device_u32(addr, L * log.V).reshape(L, log.V)
+            np.testing.assert_array_equal(got, want)
+            spans.append((t0, t1))
+            svv.svv_release(ctx.h, tk)
+        # requests overlapped on the device
+        spans.sort()
+        assert any(spans[k + 1][0] < spans[k][1] for k in range(len(spans) - 1))
+        for (t, s, b, L), want in list(zip(reqs, alone))[:2]:
+            np.testing.assert_array_equal(want, oracle.query(log, t, s, b, L))
+        svv.svv_serve_stop(ctx.h)
+
+
+def test_serve_admission_and_relaunch(svv):
+    log = W.small_rmat()
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        one = 8 * log.V * 4
+        svv.svv_serve_start(ctx.h, max_window=8, capacity=16, arena_bytes=3 * one)
+        tks = [svv.svv_submit(ctx.h, 0, 0, 0, 8) for _ in range(3)]
+        assert all(t is not None for t in tks)
+        assert svv.svv_submit(ctx.h, 0, 0, 0, 8) is None  # arena full: refused
+        want = oracle.query(log, 0, 0, 0, 8)
+        for tk in tks:
+            assert svv.svv_poll(ctx.h, tk, wait=True) == 0
+            addr, _, _ = svv.svv_ticket_info(ctx.h, tk)
+            np.testing.assert_array_equal(svv.device_u32(addr, 8 * log.V).reshape(8, log.V), want)
+            svv.svv_release(ctx.h, tk)
+        # caller-owned output; after an idle period the server is relaunched
+        time.sleep(0.5)
+        out = ctx.empty_out(5)
+        tk = svv.svv_submit(ctx.h, 2, 7, 3, 5, out=out)
+        assert svv.svv_poll(ctx.h, tk, wait=True) == 0
+        np.testing.assert_array_equal(svv.to_u32(out), oracle.query(log, 2, 7, 3, 5))
+        svv.svv_release(ctx.h, tk)
+        with pytest.raises(svv.SvvError):
+            svv.svv_submit(ctx.h, 0, 0, 0, 9)  # longer than max_window
+        svv.svv_serve_stop(ctx.h)
