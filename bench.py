@@ -43,7 +43,11 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["svv", "reference"], default="svv")
-    p.add_argument("--workload", choices=["rmat20", "small"], default="rmat20")
+    p.add_argument("--workload", choices=["rmat20", "small", "batch22", "batch16", "rmat24", "serve22", "serve16"],
+                   default="rmat20",
+                   help="rmat20: the headline line; batch*: many mixed queries in one launch; rmat24: the "
+                        "two-mask-word scale-24 graph; serve*: Poisson request streams")
+    p.add_argument("--serve-seconds", type=float, default=10.0)
     p.add_argument("--plain-steps", type=int, default=1, help="timed steps of the plain recompute (0 = skip)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -262,11 +266,230 @@ def run_reference(args, world, rank):
     return 0
 
 
+def _setup_ctx(svv, log, dev, args):
+    rp, col, w, mask = svv.svv_build_versioned_csr(log.V, log.S, log.src, log.dst, log.w, log.t_add, log.t_del)
+    ctx = svv.Context(dev)
+    ctx.load_csr(log.V, log.S, rp, col, w, mask)
+    for kv in args.tune:
+        k, v = kv.split("=", 1)
+        ctx.set_tuning(k, int(v))
+    return ctx
+
+
+def _clocks_start(rank, args, dev):
+    s = ClockSampler(gpu_id_of(dev)) if (rank == 0 and not args.no_clocks) else None
+    if s:
+        s.start()
+    return s
+
+
+def run_batch(args, world, rank, local):
+    """Many mixed queries (1/3 each type, uniform sources, window lengths
+    uniform in [8, 64] at uniform offsets) answered by ONE svv_query_batch
+    launch; one step = the whole batch."""
+    import torch
+
+    import __graft_entry__
+    from paper_2502_10579_gb300 import svv
+    dev = local
+    torch.cuda.set_device(dev)
+    __graft_entry__.build()
+    if args.workload == "batch22":
+        log, nq = W.rmat22(), 256
+        desc = "RMAT scale 22 (V=4,194,304, E0=67,108,864) w[1,999] S=64, 0.05% churn/step; 256 mixed queries, L in [8,64]"
+    else:
+        log, nq = W.scaled_rmat(16, 16, 64, 0.0005, 1016), 64
+        desc = "RMAT scale 16 (V=65,536, E0=1,048,576) w[1,999] S=64, 0.05% churn/step; 64 mixed queries, L in [8,64]"
+    qs = W.batch_queries(log, n=nq, seed=3)
+    ctx = _setup_ctx(svv, log, dev, args)
+    outs = [ctx.empty_out(q.win_len) for q in qs]
+    specs = [(q.type, q.source, q.win_begin, q.win_len, o) for q, o in zip(qs, outs)]
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(1, args.warmup)):
+        st = svv.svv_query_batch(ctx.h, specs, stream)
+        assert all(x == 0 for x in st), st
+    torch.cuda.synchronize()
+    sampler = _clocks_start(rank, args, dev)
+    barrier(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(args.steps):
+        ev0.record(stream)
+        svv.svv_query_batch(ctx.h, specs, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms += ev0.elapsed_time(ev1)
+    clocks = sampler.stop() if sampler else None
+    ms = max_over_ranks(ms, world, f"cuda:{dev}")
+    vals = sum(q.win_len * log.V for q in qs)
+    value = vals * args.steps * world / (ms / 1e3)
+    stats = ctx.stats()
+    # the same queries one at a time through svv_query, and a sample of the
+    # plain per-snapshot recompute
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for q, o in zip(qs, outs):
+        ctx.query(q.type, q.source, q.win_begin, q.win_len, out=o, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    sample = qs[:6]
+    e0.record(stream)
+    for q in sample:
+        ctx.query(q.type, q.source, q.win_begin, q.win_len, stream=stream, plain=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    plain_value = sum(q.win_len * log.V for q in sample) / (plain_ms / 1e3)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "snapshot x vertex values/s (batched intersection-union queries, one launch)",
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": desc, "queries": nq, "output_bytes": int(vals * 4), "teams": stats["batch_teams"],
+                       "team_blocks": stats["batch_team_blocks"],
+                       "tuning": dict(kv.split("=", 1) for kv in args.tune)},
+            "one_at_a_time": {"value": vals / (seq_ms / 1e3), "unit": UNIT, "ms": seq_ms},
+            "plain_sample": {"value": plain_value, "unit": UNIT, "queries": len(sample), "ms": plain_ms},
+            "clocks": clocks, "gpu_launches": args.steps}), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_rmat24(args, world, rank, local):
+    """RMAT scale 24, 100 snapshots (two mask words), SSSP and BFS from 16
+    sources at windows of 25, 50 and 100 snapshots, one query at a time."""
+    import torch
+
+    import __graft_entry__
+    from paper_2502_10579_gb300 import svv
+    dev = local
+    torch.cuda.set_device(dev)
+    __graft_entry__.build()
+    t0 = time.perf_counter()
+    log = W.rmat24()
+    gen_s = time.perf_counter() - t0
+    qs = W.rmat24_queries(log)
+    ctx = _setup_ctx(svv, log, dev, args)
+    ctx.set_tuning("phase_timing", 1)
+    out = ctx.empty_out(max(q.win_len for q in qs))
+    stream = torch.cuda.current_stream(dev)
+    for q in qs[:2]:
+        ctx.query(q.type, q.source, q.win_begin, q.win_len, out=out[: q.win_len], stream=stream)
+    torch.cuda.synchronize()
+    sampler = _clocks_start(rank, args, dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per = []
+    for q in qs:
+        e0.record(stream)
+        ctx.query(q.type, q.source, q.win_begin, q.win_len, out=out[: q.win_len], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = ctx.stats()
+        per.append((q.type, q.win_len, e0.elapsed_time(e1), st["unstable"], st["qrs_edges"]))
+    clocks = sampler.stop() if sampler else None
+    ms = sum(p[2] for p in per)
+    vals = sum(q.win_len * log.V for q in qs)
+    by = {}
+    for t, L, m, u, eq in per:
+        k = f"{W.TYPE_NAMES[t]}_L{L}"
+        by.setdefault(k, []).append(m)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "snapshot x vertex values/s (intersection-union path, scale-24 graph)",
+            "value": vals * world / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": len(qs), "warmup": 2,
+            "ms_per_step": ms / len(qs), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "RMAT scale 24 (V=16,777,216, E0=268,435,456) w[1,999] S=100 (2 mask words), "
+                                   "0.1% degree-skewed churn/step; SSSP+BFS x 16 sources x L in {25,50,100}",
+                       "generate_s": gen_s, "edges": ctx.graph.E},
+            "ms_by_query_kind": {k: statistics.median(v) for k, v in by.items()},
+            "clocks": clocks, "gpu_launches": 5 * len(qs)}), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_serve(args, world, rank, local):
+    """Poisson request streams at 100, 1,000 and 10,000 requests/s (type
+    uniform, source uniform, L uniform in [8, 100] at a uniform offset) served
+    by the live batch kernel with arena admission; the plain per-snapshot
+    recompute served FIFO on the first requests of the 100/s stream."""
+    import torch
+
+    import __graft_entry__
+    from paper_2502_10579_gb300 import svv
+    dev = local
+    torch.cuda.set_device(dev)
+    __graft_entry__.build()
+    if args.workload == "serve22":
+        log = W.rmat22(seed=1005, n_snapshots=128)
+        desc = "RMAT scale 22 (V=4,194,304, E0=67,108,864) w[1,999] S=128, 0.05% churn/step"
+    else:
+        log = W.scaled_rmat(16, 16, 128, 0.0005, 1016)
+        desc = "RMAT scale 16 (V=65,536, E0=1,048,576) w[1,999] S=128, 0.05% churn/step"
+    ctx = _setup_ctx(svv, log, dev, args)
+    arena = (64 << 30) if args.workload == "serve22" else (2 << 30)
+    svv.svv_serve_start(ctx.h, max_window=min(100, log.S), capacity=1 << 16, arena_bytes=arena)
+    dur = args.serve_seconds
+    warm = 1.0
+    results = {}
+    for rate in (100, 1000, 10000):
+        # a saturated stream only grows its backlog: cap each stream at about
+        # 2,500 requests; the first 10% are warm-up and not measured
+        d = min(dur + warm, 2500.0 / rate)
+        reqs = W.serve_requests(log, rate, d, seed=5)
+        warm = 0.1 * d
+        lat, done = svv.svv_serve_replay(ctx.h, [(a, q.type, q.source, q.win_begin, q.win_len) for a, q in reqs])
+        arr = np.array([a for a, _ in reqs])
+        meas = arr >= warm
+        span = (done[meas].max() - warm) if meas.any() else 1.0
+        vals = sum(q.win_len * log.V for (a, q), m in zip(reqs, meas) if m)
+        results[str(rate)] = {"requests": int(meas.sum()), "p50_ms": float(np.percentile(lat[meas], 50)),
+                              "p99_ms": float(np.percentile(lat[meas], 99)),
+                              "throughput_rps": float(meas.sum() / span), "values_per_s": vals / span}
+    svv.svv_serve_stop(ctx.h)
+    # plain per-snapshot recompute served FIFO, first requests of the 100/s stream
+    reqs = W.serve_requests(log, 100, 1.0, seed=5)[:12]
+    out = ctx.empty_out(min(100, log.S))
+    t_start = time.perf_counter()
+    lat = []
+    for arr, q in reqs:
+        while time.perf_counter() - t_start < arr:
+            time.sleep(0.0001)
+        ctx.query(q.type, q.source, q.win_begin, q.win_len, out=out[: q.win_len], plain=True)
+        torch.cuda.synchronize()
+        lat.append(1e3 * (time.perf_counter() - t_start - arr))
+    span = time.perf_counter() - t_start - reqs[0][0]
+    plain = {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+             "throughput_rps": len(reqs) / span,
+             "values_per_s": sum(q.win_len * log.V for _, q in reqs) / span}
+    if rank == 0:
+        best = max(results.values(), key=lambda r: r["values_per_s"])
+        print(json.dumps({
+            "metric": "served requests: p50/p99 latency ms and throughput under Poisson arrivals",
+            "value": best["values_per_s"], "unit": UNIT, "n_gpus": world, "steps": sum(r["requests"] for r in results.values()),
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": desc + f"; Poisson 100/1,000/10,000 req/s, each stream min({dur:g} s, 2,500 requests), "
+                                   "first 10% excluded",
+                       "arena_bytes": arena, "admission": "output arena (svv_submit refuses when full)"},
+            "serve": results, "plain_fifo": plain}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload in ("batch22", "batch16"):
+        return run_batch(args, world, rank, local)
+    if args.workload == "rmat24":
+        return run_rmat24(args, world, rank, local)
+    if args.workload in ("serve22", "serve16"):
+        return run_serve(args, world, rank, local)
 
     import torch
 

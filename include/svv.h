@@ -184,6 +184,15 @@ svv_status svv_ticket_info(svv_ctx *ctx, uint64_t ticket, uint32_t **out,
 /* Free a finished request's slot and arena space (SVV_EBUSY while running). */
 svv_status svv_release(svv_ctx *ctx, uint64_t ticket);
 
+/* Load driver for measurement: serve n requests that arrive at arrival_s[k]
+ * seconds after the call starts (non-decreasing), each submitted at its arrival
+ * time or, if the server refuses it, as soon as room frees up (arrival order).
+ * latency_ms[k] receives completion minus arrival, done_s[k] (may be NULL) the
+ * completion time.  Returns when every request is done: SVV_OK, or the first
+ * failing request status. */
+svv_status svv_serve_replay(svv_ctx *ctx, uint32_t n, const svv_query_spec *specs,
+                            const double *arrival_s, double *latency_ms, double *done_s);
+
 /* Stop the server (pending requests are abandoned) and free its memory. */
 svv_status svv_serve_stop(svv_ctx *ctx);
 

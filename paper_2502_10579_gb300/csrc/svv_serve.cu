@@ -277,6 +277,66 @@ svv_status svv_release(svv_ctx* c, uint64_t ticket) {
   return SVV_OK;
 }
 
+svv_status svv_serve_replay(svv_ctx* c, uint32_t n, const svv_query_spec* specs, const double* arrival_s,
+                            double* latency_ms, double* done_s) {
+  if (!c || (n && (!specs || !arrival_s || !latency_ms))) return SVV_EINVAL;
+  ServeState& v = c->serve;
+  if (!v.active) return fail(c, SVV_EINVAL, "serving not started");
+  using clk = std::chrono::steady_clock;
+  std::vector<uint64_t> ticket(n, 0);
+  std::vector<uint8_t> state(n, 0);  // 0 waiting, 1 submitted, 2 done
+  std::deque<uint32_t> inflight;     // submitted, in submission order
+  uint32_t next_arrival = 0, ndone = 0;
+  svv_status worst = SVV_OK;
+  const auto t0 = clk::now();
+  auto now_s = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+  std::deque<uint32_t> arrived;  // arrived, not yet admitted
+  while (ndone < n) {
+    const double t = now_s();
+    while (next_arrival < n && arrival_s[next_arrival] <= t) arrived.push_back(next_arrival++);
+    // admit in arrival order while there is room
+    while (!arrived.empty()) {
+      const uint32_t k = arrived.front();
+      uint64_t tk = 0;
+      svv_status st = svv_submit(c, &specs[k], &tk);
+      if (st == SVV_EBUSY) break;
+      if (st) return st;
+      ticket[k] = tk;
+      state[k] = 1;
+      inflight.push_back(k);
+      arrived.pop_front();
+    }
+    // completions (device flags in mapped memory)
+    bool any = false;
+    for (auto it = inflight.begin(); it != inflight.end();) {
+      const uint32_t k = *it;
+      const uint32_t slot = (uint32_t)(ticket[k] % v.cap);
+      if (reinterpret_cast<volatile uint32_t*>(v.h_done)[slot]) {
+        std::atomic_thread_fence(std::memory_order_acquire);
+        const double td = now_s();
+        latency_ms[k] = 1e3 * (td - arrival_s[k]);
+        if (done_s) done_s[k] = td;
+        const svv_status rs = status_of(reinterpret_cast<volatile uint32_t*>(v.h_qerr)[slot], 1u);
+        if (rs && !worst) worst = rs;
+        svv_release(c, ticket[k]);
+        state[k] = 2;
+        ndone++;
+        it = inflight.erase(it);
+        any = true;
+      } else {
+        ++it;
+      }
+    }
+    if (!any && !inflight.empty()) {
+      DeviceGuard dg(c->device);
+      svv_status st = ensure_running(c);
+      if (st) return st;
+    }
+    if (now_s() > (n ? arrival_s[n - 1] : 0.0) + 600.0) return fail(c, SVV_ETIMEOUT, "replay did not finish");
+  }
+  return worst;
+}
+
 svv_status svv_serve_stop(svv_ctx* c) {
   if (!c) return SVV_EINVAL;
   if (!c->serve.active) return SVV_OK;

@@ -24,7 +24,7 @@ EXPORTS = ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "sv
            "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats", "svv_device_bytes", "svv_status_str",
            "svv_last_error", "svv_destroy", "svv_solve_snapshot_noalloc",
            "svv_get_round_trace", "svv_query_batch", "svv_serve_start", "svv_submit", "svv_poll",
-           "svv_ticket_info", "svv_release", "svv_serve_stop")
+           "svv_ticket_info", "svv_release", "svv_serve_stop", "svv_serve_replay")
 
 
 class SvvError(RuntimeError):
@@ -92,7 +92,9 @@ def lib():
     L.svv_ticket_info.argtypes = [P, u64, ctypes.POINTER(P), ctypes.POINTER(u64), ctypes.POINTER(u64)]
     L.svv_release.argtypes = [P, u64]
     L.svv_serve_stop.argtypes = [P]
-    for f in ("svv_serve_start", "svv_submit", "svv_poll", "svv_ticket_info", "svv_release", "svv_serve_stop"):
+    L.svv_serve_replay.argtypes = [P, u32, ctypes.POINTER(svv_query_spec), P, P, P]
+    for f in ("svv_serve_start", "svv_submit", "svv_poll", "svv_ticket_info", "svv_release", "svv_serve_stop",
+              "svv_serve_replay"):
         getattr(L, f).restype = i32
     for f in ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "svv_query_plain",
               "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats"):
@@ -254,6 +256,21 @@ def svv_ticket_info(ctx, ticket: int):
 
 def svv_release(ctx, ticket: int):
     _check(ctx, lib().svv_release(ctx, ticket))
+
+
+def svv_serve_replay(ctx, requests):
+    """requests: list of (arrival_s, type, source, win_begin, win_len).  Returns
+    (latency_ms, done_s) numpy arrays; outputs come from the server's arena."""
+    n = len(requests)
+    arr = (svv_query_spec * max(n, 1))()
+    at = np.zeros(max(n, 1), np.float64)
+    for i, (a, t, s, b, L) in enumerate(requests):
+        arr[i].type, arr[i].source, arr[i].win_begin, arr[i].win_len, arr[i].out = t, s, b, L, None
+        at[i] = a
+    lat = np.zeros(max(n, 1), np.float64)
+    done = np.zeros(max(n, 1), np.float64)
+    _check(ctx, lib().svv_serve_replay(ctx, n, arr, _ptr(at), _ptr(lat), _ptr(done)))
+    return lat[:n], done[:n]
 
 
 def svv_serve_stop(ctx):

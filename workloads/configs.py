@@ -90,3 +90,39 @@ def batch_queries(log: EdgeLog, n: int = 256, seed: int = 3, l_lo: int = 8, l_hi
         b = int(rng.integers(0, log.S - L + 1))
         out.append(Query(int(t), src, b, L))
     return out
+
+
+def rmat24_queries(log: EdgeLog, n_sources: int = 16, seed: int = 4, windows=(25, 50, 100)):
+    """SSSP and BFS from n_sources sources (uniform among vertices with
+    out-degree > 0 in G_0) over the windows [0, L): 2 * n_sources * len(windows)
+    queries, run one at a time."""
+    rng = np.random.default_rng(seed)
+    deg = np.bincount(log.src[: log.n_base].astype(np.int64), minlength=log.V)
+    cand = np.flatnonzero(deg > 0)
+    srcs = cand[rng.integers(0, cand.shape[0], size=n_sources)]
+    out = []
+    for s in srcs.tolist():
+        for L in windows:
+            L = min(L, log.S)
+            out.append(Query(SSSP, int(s), 0, L))
+            out.append(Query(BFS, int(s), 0, L))
+    return out
+
+
+def serve_requests(log: EdgeLog, rate: float, duration_s: float, seed: int = 5, l_lo: int = 8,
+                   l_hi: int = 100):
+    """Poisson arrivals at `rate` per second over `duration_s`: a list of
+    (arrival_s, Query) with the type uniform over SSSP/SSWP/BFS, a uniform
+    source, a window length uniform in [l_lo, l_hi] at a uniform offset."""
+    rng = np.random.default_rng(seed)
+    l_hi = min(l_hi, log.S)
+    t = 0.0
+    out = []
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= duration_s:
+            break
+        L = int(rng.integers(l_lo, l_hi + 1))
+        b = int(rng.integers(0, log.S - L + 1))
+        out.append((t, Query(int(rng.integers(0, 3)), int(rng.integers(0, log.V)), b, L)))
+    return out
