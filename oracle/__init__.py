@@ -6,9 +6,10 @@ it, and it imports nothing from the library.
 
 ``oracle.c`` solves each snapshot of a window from scratch on the snapshot
 materialised by replaying the edge log (paper Section 2, Fig. 2a): binary-heap
-Dijkstra for SSSP, widest-path Dijkstra for SSWP and a FIFO BFS (Table 2).
+Dijkstra for SSSP, widest-path Dijkstra for SSWP, a FIFO BFS and narrowest-path
+Dijkstra for SSNP (Table 2).
 ``bounds()`` solves the intersection and union graphs of a window (Section 3,
-Step 1).  Value encoding: SSSP/BFS unreachable = 0xFFFFFFFF; SSWP source =
+Step 1).  Value encoding: SSSP/BFS/SSNP unreachable = 0xFFFFFFFF; SSWP source =
 0xFFFFFFFF (+inf) and unreachable = 0; SSSP sums saturate at 0xFFFFFFFE.
 
 Every function is pinned by ``tests/test_oracle_pins.py`` (Floyd-Warshall
@@ -24,7 +25,7 @@ import threading
 
 import numpy as np
 
-SSSP, SSWP, BFS = 0, 1, 2
+SSSP, SSWP, BFS, SSNP = 0, 1, 2, 3
 INF = 0xFFFFFFFF
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

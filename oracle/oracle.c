@@ -14,13 +14,15 @@
  *   SSSP : Val(v) = min over in-edges (u,v) of Val(u) + w(u,v); Val(src) = 0.
  *   SSWP : Val(v) = max over in-edges of min(Val(u), w(u,v));  Val(src) = +inf.
  *   BFS  : Val(v) = min over in-edges of Val(u) + 1;          Val(src) = 0.
+ *   SSNP : Val(v) = min over in-edges of max(Val(u), w(u,v)); Val(src) = 0.
  * Readings where the paper is silent (unreachable encoding, overflow):
  *   SSSP/BFS unreachable = 0xFFFFFFFF; SSWP +inf = 0xFFFFFFFF and unreachable
  *   = 0; SSSP sums saturate at 0xFFFFFFFE so a reached vertex never reads as
  *   unreachable.
  *
  * Solvers: binary-heap Dijkstra (SSSP), max-heap widest-path Dijkstra (SSWP),
- * FIFO breadth-first search (BFS).
+ * FIFO breadth-first search (BFS), min-heap narrowest-path Dijkstra (SSNP: the
+ * path value is the largest weight on the path).
  *
  * Extras used to pin single steps of the method (Section 3, Step 1):
  * oracle_bounds() materialises the intersection graph (instances live in every
@@ -35,6 +37,7 @@
 #define OR_SSSP 0
 #define OR_SSWP 1
 #define OR_BFS 2
+#define OR_SSNP 3
 #define OR_INF 0xFFFFFFFFu
 #define OR_SAT 0xFFFFFFFEu
 
@@ -163,6 +166,39 @@ oom:
     return -1;
 }
 
+/* Narrowest path, Table 2 SSNP: Val(src)=0, relax max(Val(u), w); a
+ * min-heap settles vertices in order of their path's largest weight. */
+static int solve_ssnp(uint32_t V, const uint64_t *rp, const uint32_t *col, const uint32_t *w,
+                      uint32_t src, uint32_t *best) {
+    heap h = {0};
+    h.maxheap = 0;
+    char *done = (char *)calloc(V ? V : 1, 1);
+    if (!done) return -1;
+    for (uint32_t v = 0; v < V; ++v) best[v] = OR_INF;
+    best[src] = 0;
+    if (h_push(&h, (hitem){0, src})) goto oom;
+    while (h.n) {
+        hitem t = h_pop(&h);
+        if (done[t.v] || t.key != best[t.v]) continue;
+        done[t.v] = 1;
+        for (uint64_t e = rp[t.v]; e < rp[t.v + 1]; ++e) {
+            uint32_t nb = t.key > w[e] ? t.key : w[e];
+            uint32_t x = col[e];
+            if (nb < best[x]) {
+                best[x] = nb;
+                if (h_push(&h, (hitem){nb, x})) goto oom;
+            }
+        }
+    }
+    free(h.a);
+    free(done);
+    return 0;
+oom:
+    free(h.a);
+    free(done);
+    return -1;
+}
+
 /* Breadth-first search, Table 2 BFS: level(src)=0, relax Val(u)+1. */
 static int solve_bfs(uint32_t V, const uint64_t *rp, const uint32_t *col, uint32_t src,
                      uint32_t *level) {
@@ -195,6 +231,7 @@ int oracle_solve(int type, uint32_t V, const uint64_t *row_ptr, const uint32_t *
     case OR_SSSP: return solve_sssp(V, row_ptr, col, w, src, out);
     case OR_SSWP: return solve_sswp(V, row_ptr, col, w, src, out);
     case OR_BFS: return solve_bfs(V, row_ptr, col, src, out);
+    case OR_SSNP: return solve_ssnp(V, row_ptr, col, w, src, out);
     default: return -2;
     }
 }
@@ -332,7 +369,7 @@ int oracle_query(int type, uint32_t V, uint32_t S, uint64_t n_inst, const uint32
                  const int64_t *del_off, const int64_t *del_ids, uint32_t source,
                  uint32_t win_begin, uint32_t win_len, uint32_t *out, int nthreads) {
     if (source >= V || win_len == 0 || (uint64_t)win_begin + win_len > S) return -2;
-    if (type < 0 || type > 2) return -2;
+    if (type < 0 || type > 3) return -2;
     edge_log lg = {V, S, n_inst, src, dst, w, add_off, del_off, del_ids};
     if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
     if (nthreads < 1) nthreads = 1;
@@ -368,7 +405,7 @@ int oracle_bounds(int type, uint32_t V, uint32_t S, uint64_t n_inst, const uint3
                   const int64_t *del_off, const int64_t *del_ids, uint32_t source,
                   uint32_t win_begin, uint32_t win_len, uint32_t *r_cap, uint32_t *r_cup) {
     if (source >= V || win_len == 0 || (uint64_t)win_begin + win_len > S) return -2;
-    if (type < 0 || type > 2) return -2;
+    if (type < 0 || type > 3) return -2;
     edge_log lg = {V, S, n_inst, src, dst, w, add_off, del_off, del_ids};
     size_t n = n_inst ? n_inst : 1;
     unsigned char *alive = (unsigned char *)malloc(n);

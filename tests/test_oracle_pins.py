@@ -1,10 +1,11 @@
 """Pins for the CPU oracle, against things other than itself.
 
-* Floyd-Warshall brute force (min-plus, max-min, unit min-plus) on random
+* Floyd-Warshall brute force (min-plus, max-min, unit min-plus, min-max) on random
   multigraphs of <= 64 vertices with self-loops, sinks and unreachable parts.
 * SciPy's Dijkstra / unweighted shortest paths on a 4,096-vertex RMAT snapshot.
 * Widest path as a threshold-reachability closed form: the width of v is the
-  largest t such that v is reachable from the source over edges of weight >= t.
+  largest t such that v is reachable from the source over edges of weight >= t;
+  narrowest path likewise: the smallest t with v reachable over weights <= t.
 * A pure-Python set replay of the edge log.
 * Theorem 1 / Table 1 bounds and Theorem 2 (paper Section 3).
 * Special cases (window of one snapshot, no deltas, isolated source, saturation).
@@ -36,6 +37,14 @@ def _csr(V, src, dst, w):
 def _fw(V, src, dst, w, kind):
     """Floyd-Warshall over the semiring of the query; returns V x V."""
     big = np.int64(1) << 40
+    if kind == "ssnp":  # min-max semiring
+        D = np.full((V, V), big, np.int64)
+        for u, v, x in zip(src, dst, w.astype(np.int64)):
+            D[u, v] = min(D[u, v], x)
+        np.fill_diagonal(D, 0)
+        for k in range(V):
+            D = np.minimum(D, np.maximum(D[:, k:k + 1], D[k:k + 1, :]))
+        return np.where(D >= big, INF, D).astype(np.uint64)
     if kind in ("sssp", "bfs"):
         D = np.full((V, V), big, np.int64)
         ww = np.ones_like(w, dtype=np.int64) if kind == "bfs" else w.astype(np.int64)
@@ -68,7 +77,8 @@ def _random_graph(rng, V, m, w_hi=50):
     return src, dst, w
 
 
-@pytest.mark.parametrize("kind,qtype", [("sssp", oracle.SSSP), ("sswp", oracle.SSWP), ("bfs", oracle.BFS)])
+@pytest.mark.parametrize("kind,qtype", [("sssp", oracle.SSSP), ("sswp", oracle.SSWP), ("bfs", oracle.BFS),
+                                        ("ssnp", oracle.SSNP)])
 @pytest.mark.parametrize("seed", range(6))
 def test_floyd_warshall(kind, qtype, seed):
     rng = np.random.default_rng(100 + seed)
@@ -130,6 +140,24 @@ def test_widest_path_threshold_closed_form(small_log):
         np.testing.assert_array_equal(got, ref)
 
 
+def test_narrowest_path_threshold_closed_form(small_log):
+    """SSNP value of v = the smallest t such that v is reachable from the
+    source over edges of weight <= t (the source itself is 0)."""
+    V = small_log.V
+    rp, col, w = oracle.snapshot_csr(small_log, 4)
+    rows = np.repeat(np.arange(V), np.diff(rp.astype(np.int64)))
+    for s in (0, 9):
+        ref = np.full(V, INF, np.uint64)
+        for t in np.unique(w)[::-1]:  # descending, so later (smaller) t overwrite
+            keep = w <= t
+            A = sp.csr_matrix((np.ones(keep.sum()), (rows[keep], col[keep])), shape=(V, V))
+            reach = csgraph.breadth_first_order(A, s, directed=True, return_predecessors=False)
+            ref[reach] = t
+        ref[s] = 0
+        got = oracle.solve(oracle.SSNP, V, rp, col, w, s).astype(np.uint64)
+        np.testing.assert_array_equal(got, ref)
+
+
 def test_replay_matches_python_sets():
     for seed in range(3):
         log = W.random_small_log(seed, V=40, n_edges=120, S=6, n_add=9, n_del=7)
@@ -164,7 +192,7 @@ def _check_theorems(log, qtype, src, b, L):
     return vals, cap, cup, stable, uvv
 
 
-@pytest.mark.parametrize("qtype", [oracle.SSSP, oracle.SSWP, oracle.BFS])
+@pytest.mark.parametrize("qtype", [oracle.SSSP, oracle.SSWP, oracle.BFS, oracle.SSNP])
 def test_theorems_small_rmat(small_log, qtype):
     for b, L in [(0, 8), (2, 5), (7, 1)]:
         vals, cap, cup, stable, uvv = _check_theorems(small_log, qtype, 0, b, L)
@@ -179,7 +207,7 @@ def test_theorems_random(seed):
     log = W.random_small_log(seed, V=int(rng.integers(8, 60)), n_edges=int(rng.integers(20, 200)),
                              S=int(rng.integers(1, 10)), n_add=int(rng.integers(0, 12)),
                              n_del=int(rng.integers(0, 12)))
-    for qtype in (oracle.SSSP, oracle.SSWP, oracle.BFS):
+    for qtype in (oracle.SSSP, oracle.SSWP, oracle.BFS, oracle.SSNP):
         L = int(rng.integers(1, log.S + 1))
         b = int(rng.integers(0, log.S - L + 1))
         _check_theorems(log, qtype, int(rng.integers(0, log.V)), b, L)
@@ -187,7 +215,7 @@ def test_theorems_random(seed):
 
 def test_no_deltas_everything_stable():
     log = W.random_small_log(5, V=50, n_edges=300, S=4, n_add=0, n_del=0)
-    for qtype in (oracle.SSSP, oracle.SSWP, oracle.BFS):
+    for qtype in (oracle.SSSP, oracle.SSWP, oracle.BFS, oracle.SSNP):
         vals, cap, cup, stable, _ = _check_theorems(log, qtype, 3, 0, 4)
         assert stable.all()
         assert (vals == cap[None]).all()
@@ -199,7 +227,7 @@ def test_isolated_source():
     keep = (log.src != iso)
     # re-route every out-edge of vertex 29 so it has none in any snapshot
     log.src = np.where(keep, log.src, 0).astype(np.uint32)
-    for qtype, unreached in ((oracle.SSSP, INF), (oracle.SSWP, 0), (oracle.BFS, INF)):
+    for qtype, unreached in ((oracle.SSSP, INF), (oracle.SSWP, 0), (oracle.BFS, INF), (oracle.SSNP, INF)):
         vals = oracle.query(log, qtype, iso, 0, 3)
         other = np.arange(log.V) != iso
         assert (vals[:, other] == unreached).all()
@@ -240,7 +268,8 @@ def _golden_log():
     return g, lg
 
 
-@pytest.mark.parametrize("name,qtype", [("sssp", oracle.SSSP), ("sswp", oracle.SSWP), ("bfs", oracle.BFS)])
+@pytest.mark.parametrize("name,qtype", [("sssp", oracle.SSSP), ("sswp", oracle.SSWP), ("bfs", oracle.BFS),
+                                        ("ssnp", oracle.SSNP)])
 def test_golden_vertex_c(name, qtype):
     g, lg = _golden_log()
     exp = g["expected"][name]
@@ -263,3 +292,5 @@ def test_bad_arguments_rejected():
         oracle.query(lg, oracle.SSSP, 0, 1, 2)
     with pytest.raises(ValueError):
         oracle.query(lg, 7, 0, 0, 1)
+    with pytest.raises(ValueError):
+        oracle.query(lg, 4, 0, 0, 1)

@@ -12,8 +12,8 @@ import numpy as np
 
 from .rmat import EdgeLog, make_log, max_out_degree_vertex
 
-SSSP, SSWP, BFS = 0, 1, 2
-TYPE_NAMES = {SSSP: "sssp", SSWP: "sswp", BFS: "bfs"}
+SSSP, SSWP, BFS, SSNP = 0, 1, 2, 3
+TYPE_NAMES = {SSSP: "sssp", SSWP: "sswp", BFS: "bfs", SSNP: "ssnp"}
 
 
 @dataclass
