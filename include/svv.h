@@ -28,6 +28,8 @@
  *   - Values are uint32.  SSSP: distance, source 0, unreachable 0xFFFFFFFF,
  *     sums saturate at 0xFFFFFFFE.  BFS: hop count, source 0, unreachable
  *     0xFFFFFFFF.  SSWP: width, source 0xFFFFFFFF (+inf), unreachable 0.
+ *     SSNP: the smallest possible largest weight on a path, source 0,
+ *     unreachable 0xFFFFFFFF (Table 1: bounds as for SSSP).
  *     (Table 2 edge functions; the paper leaves the encodings unstated.)
  *   - Output layout: out[i*V + v] is the value of v in snapshot win_begin+i,
  *     for 0 <= i < win_len (snapshot-major, win_len x V).
@@ -47,7 +49,7 @@ extern "C" {
 
 typedef struct svv_ctx svv_ctx; /* opaque, owned by the library */
 
-typedef enum { SVV_SSSP = 0, SVV_SSWP = 1, SVV_BFS = 2 } svv_type;
+typedef enum { SVV_SSSP = 0, SVV_SSWP = 1, SVV_BFS = 2, SVV_SSNP = 3 } svv_type;
 
 typedef enum {
     SVV_OK = 0,
@@ -226,6 +228,7 @@ svv_status svv_get_bounds(svv_ctx *ctx, uint32_t *cap, uint32_t *cup, uint32_t *
  * same values as row snapshot-win_begin of svv_query_plain).  No context is
  * needed: the call runs on the calling thread's current CUDA device, ordered
  * on `cuda_stream`, and returns once the result is in `out`.
+ * Types SSSP, SSWP and BFS (SSNP gets SVV_EINVAL).
  * Working memory is a fixed 32 MiB device array inside the library, held by
  * every GPU that loads it until the process exits; a graph whose
  * 4*V + 16*(V + E/64 + 64) bytes (plus 1 KiB) exceed it is rejected with
@@ -251,6 +254,24 @@ svv_status svv_solve_snapshot_noalloc(svv_type type, uint32_t V, uint64_t E, uin
 svv_status svv_get_round_trace(svv_ctx *ctx, uint32_t phase, uint64_t *out, uint32_t cap,
                                uint32_t *n_out);
 
+/* Result of svv_autotune: the knobs chosen for one query type. */
+typedef struct {
+    uint32_t solve_chunk, blocks_per_sm, relax_lanes, skip_same;
+    float best_ms, default_ms;  /* probe query time with the chosen and the default knobs */
+    uint32_t candidates;        /* configurations timed */
+} svv_tune_result;
+
+/* Autotuner: times a probe query (type, source, window) under every candidate
+ * of a grid of launch knobs -- edges per work unit of the solves (two sizes at
+ * or above the loaded one), CTAs per SM (occupancy limit, 2, 3), lanes per
+ * edge in the relaxation (32, 16), per-chunk skipping of already-relaxed work
+ * (on, off) -- `reps` timed runs each after one warm-up (0 = 3), and keeps the
+ * fastest for that query type: later svv_query / svv_query_plain calls of the
+ * type use it (results are identical for every candidate).  The probe output
+ * goes to a library buffer of win_len*V uint32.  `out` may be NULL. */
+svv_status svv_autotune(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
+                        uint32_t win_len, uint32_t reps, svv_tune_result *out);
+
 /* Tuning knobs, by name: "max_iters" (frontier-round cap per solve, 0 = V+2),
  * "spin_limit_ms" (bound on every device-side wait, default 1000),
  * "solve_chunk" / "relax_chunk" / "qrs_chunk" (edges per work unit, powers of
@@ -258,7 +279,10 @@ svv_status svv_get_round_trace(svv_ctx *ctx, uint32_t phase, uint64_t *out, uint
  * (near-far width of the SSSP / SSWP solves: a frontier round relaxes only the
  * vertices within this distance of the round's best value and keeps the rest
  * queued; 0 relaxes every queued vertex; results are identical either way),
- * "batch_teams" (teams of svv_query_batch, 1..64, default 8), "round_trace" (1 = record, per frontier round of the intersection solve,
+ * "batch_teams" (teams of svv_query_batch and the server, 1..64; 0 = by graph
+ * size: 8 up to 1M vertices, fewer above, 1 from 8M), "relax_lanes" (8, 16, 32:
+ * lanes per edge in the relaxation), "skip_same" (1 = skip work chunks already
+ * relaxed with their vertex's current value), "round_trace" (1 = record, per frontier round of the intersection solve,
  * the union solve and the relaxation, the frontier size and a device
  * timestamp; read with svv_get_round_trace), "phase_timing" (1 = record
  * CUDA events between the phases of each query, reported by svv_get_stats).  SVV_EINVAL on an unknown key

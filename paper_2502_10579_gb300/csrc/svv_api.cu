@@ -31,9 +31,14 @@ void free_graph(svv_ctx* c) {
   c->mcap = c->valcap = c->staging_cap = 0;
 }
 
-LaunchCfg cfg_for(const svv_ctx* c, int occ) {
+Knobs knobs_of(const svv_ctx* c, int type) {
+  if (type >= 0 && type < 4 && c->has_tuned[type]) return c->tuned[type];
+  return Knobs{c->solve_cs, c->bps, c->relax_lanes, c->skip_same};
+}
+
+LaunchCfg cfg_for(const svv_ctx* c, int occ, int bps) {
   int per_sm = occ;
-  if (c->bps > 0) per_sm = std::min(per_sm, c->bps);
+  if (bps > 0) per_sm = std::min(per_sm, bps);
   per_sm = std::max(1, std::min(per_sm, 4));
   return LaunchCfg{c->num_sms * per_sm, c->threads};
 }
@@ -76,7 +81,7 @@ svv_status ensure_window(svv_ctx* c, uint32_t L) {
 svv_status check_query(svv_ctx* c, int type, uint32_t source, uint32_t wb, uint32_t wl, const void* out) {
   if (!c) return SVV_EINVAL;
   if (!c->loaded) return fail(c, SVV_ENOTLOADED, "no graph loaded");
-  if (type < 0 || type > 2) return fail(c, SVV_EINVAL, "unknown query type");
+  if (type < 0 || type > 3) return fail(c, SVV_EINVAL, "unknown query type");
   if (source >= c->g.V) return fail(c, SVV_EINVAL, "source >= V");
   if (wl == 0) return fail(c, SVV_EINVAL, "win_len == 0");
   if ((uint64_t)wb + wl > c->g.S) return fail(c, SVV_EINVAL, "win_begin + win_len > S");
@@ -84,7 +89,7 @@ svv_status check_query(svv_ctx* c, int type, uint32_t source, uint32_t wb, uint3
   return SVV_OK;
 }
 
-SolveArgs solve_base(svv_ctx* c, uint32_t wb, uint32_t wl, int type) {
+SolveArgs solve_base(svv_ctx* c, uint32_t wb, uint32_t wl, int type, const Knobs& kn) {
   SolveArgs a{};
   a.g = c->g;
   a.win = Window{wb, wl};
@@ -92,13 +97,17 @@ SolveArgs solve_base(svv_ctx* c, uint32_t wb, uint32_t wl, int type) {
   a.q0 = c->q0;
   a.q1 = c->q1;
   a.qcap = c->qcap;
-  a.cshift = c->solve_cs;
+  a.cshift = kn.solve_cs;
   a.qerr = c->qerr;
   a.delta = (type == 0 || type == 1) ? c->delta[type] : 0u;
   // deferred rounds add to the round count, so the default cap is wider
   const uint64_t cap = a.delta ? 16ull * c->g.V + 64 : (uint64_t)c->g.V + 2;
   a.maxit = c->maxit ? c->maxit : (uint32_t)std::min<uint64_t>(cap, 0xFFFFFFF0ull);
   a.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
+  if (kn.skip_same && c->procv) {
+    a.procv = c->procv;
+    a.pcap = c->g.V + (c->g.E >> kn.solve_cs) + 2u;  // chunk ids stay below this
+  }
   return a;
 }
 
@@ -225,8 +234,14 @@ svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
         if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
     }
     c->phase_timing = v != 0;
+  } else if (k == "relax_lanes") {
+    if (v != 8 && v != 16 && v != 32) return fail(c, SVV_EINVAL, "relax_lanes is 8, 16 or 32");
+    c->relax_lanes = (uint32_t)v;
+  } else if (k == "skip_same") {
+    if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "skip_same is 0 or 1");
+    c->skip_same = v != 0;
   } else if (k == "batch_teams") {
-    if (v < 1 || v > 64) return fail(c, SVV_EINVAL, "batch_teams in [1, 64]");
+    if (v < 0 || v > 64) return fail(c, SVV_EINVAL, "batch_teams in [0, 64]");
     c->batch_teams = (int)v;
   } else if (k == "round_trace") {
     if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "round_trace is 0 or 1");
@@ -404,12 +419,14 @@ svv_status svv_load(svv_ctx* c, uint32_t V, uint64_t E, uint32_t S, const uint64
       (st = alloc_n(c, c->scratch_bufs, std::max<uint32_t>(E2, 1), &c->qcw)) ||
       (st = alloc_n(c, c->scratch_bufs, qcap, &c->q0)) || (st = alloc_n(c, c->scratch_bufs, qcap, &c->q1)) ||
       (st = alloc_n(c, c->scratch_bufs, ucap, &c->units)) ||
-      (st = alloc_n(c, c->scratch_bufs, kNumCtl, &c->ctl)) || (st = alloc_n(c, c->scratch_bufs, 1, &c->qerr))) {
+      (st = alloc_n(c, c->scratch_bufs, kNumCtl, &c->ctl)) || (st = alloc_n(c, c->scratch_bufs, 1, &c->qerr)) ||
+      (st = alloc_n(c, c->scratch_bufs, (uint64_t)V + (E2 >> 4) + 64, &c->procv))) {
     free_graph(c);
     return st;
   }
   c->qcap = (uint32_t)qcap;
   c->ucap = (uint32_t)ucap;
+  c->pcap = (uint32_t)((uint64_t)V + (E2 >> 4) + 64);
   c->ecap = std::max<uint32_t>(E2, 1);
   c->g = g;
   c->loaded = true;
@@ -433,7 +450,8 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
   if (timing) cudaEventRecord(c->ev[0], s);
 
   // a1: intersection graph (edges present in every window snapshot)
-  SolveArgs a1 = solve_base(c, wb, wl, t);
+  const Knobs kn = knobs_of(c, t);
+  SolveArgs a1 = solve_base(c, wb, wl, t, kn);
   a1.init = kInitSource;
   a1.source = source;
   a1.val = c->rI;
@@ -444,11 +462,11 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
     a1.trace = c->trace;
     a1.trace_cap = kTraceCap;
   }
-  if ((e = launch_solve(t, kPredAll, a1, cfg_for(c, c->occ_solve), s)) != cudaSuccess)
+  if ((e = launch_solve(t, kPredAll, a1, cfg_for(c, c->occ_solve, kn.bps), s)) != cudaSuccess)
     return cuda_fail(c, e, "launch intersection solve");
   if (timing) cudaEventRecord(c->ev[1], s);
   // a2: union graph, incrementally from the intersection values
-  SolveArgs a2 = solve_base(c, wb, wl, t);
+  SolveArgs a2 = solve_base(c, wb, wl, t, kn);
   a2.init = kInitSeed;
   a2.source = source;
   a2.base = c->rI;
@@ -458,7 +476,7 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
     a2.trace = c->trace + kTraceCap;
     a2.trace_cap = kTraceCap;
   }
-  if ((e = launch_solve(t, kPredAny, a2, cfg_for(c, c->occ_solve), s)) != cudaSuccess)
+  if ((e = launch_solve(t, kPredAny, a2, cfg_for(c, c->occ_solve, kn.bps), s)) != cudaSuccess)
     return cuda_fail(c, e, "launch union solve");
   if (timing) cudaEventRecord(c->ev[2], s);
   // a3+a4: stable compaction and the Q-relevant subgraph
@@ -484,7 +502,7 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
   q.ctl = c->ctl + 2;
   q.qerr = c->qerr;
   q.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
-  LaunchCfg qc = cfg_for(c, c->occ_qrs);
+  LaunchCfg qc = cfg_for(c, c->occ_qrs, kn.bps);
   if ((int64_t)qc.blocks > (int64_t)c->num_sms * 4) qc.blocks = c->num_sms * 4;
   if ((e = launch_qrs(q, qc, s)) != cudaSuccess) return cuda_fail(c, e, "launch subgraph extraction");
   if (timing) cudaEventRecord(c->ev[3], s);
@@ -494,7 +512,7 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
   for (uint32_t s0 = 0; s0 < wl; s0 += kMaxSlab) {
     const uint32_t ls = std::min(kMaxSlab, wl - s0);
     uint32_t P, K;
-    slab_shape(ls, P, K);
+    slab_shape_p(ls, kn.relax_lanes, P, K);
     if (s0 > 0 && (e = cudaMemsetAsync(c->ctl + 3, 0, sizeof(TeamCtl), s)) != cudaSuccess)
       return cuda_fail(c, e, "memset");
     if (timing) cudaEventRecord(c->ev[6], s);
@@ -526,7 +544,7 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
       r.trace = c->trace + 2 * kTraceCap;
       r.trace_cap = kTraceCap;
     }
-    if ((e = launch_relax(t, P, K, r, cfg_for(c, c->occ_relax), s)) != cudaSuccess)
+    if ((e = launch_relax(t, P, K, r, cfg_for(c, c->occ_relax, kn.bps), s)) != cudaSuccess)
       return cuda_fail(c, e, "launch relaxation");
     if (timing) cudaEventRecord(c->ev[4], s);
     ScatterArgs sa{};
@@ -596,13 +614,14 @@ svv_status svv_query_plain(svv_ctx* c, svv_type type, uint32_t source, uint32_t 
     TeamCtl* slot = c->ctl + 8 + (i % (kNumCtl - 8));
     if (i >= (uint32_t)(kNumCtl - 8) && (e = cudaMemsetAsync(slot, 0, sizeof(TeamCtl), s)) != cudaSuccess)
       return cuda_fail(c, e, "memset");
-    SolveArgs a = solve_base(c, wb, wl, (int)type);
+    SolveArgs a = solve_base(c, wb, wl, (int)type, knobs_of(c, (int)type));
     a.init = kInitSource;
     a.source = source;
     a.bit = wb + i;
     a.val = out + (size_t)i * c->g.V;
     a.ctl = slot;
-    if ((e = launch_solve((int)type, kPredBit, a, cfg_for(c, c->occ_solve), s)) != cudaSuccess)
+    if ((e = launch_solve((int)type, kPredBit, a, cfg_for(c, c->occ_solve, knobs_of(c, (int)type).bps), s)) !=
+        cudaSuccess)
       return cuda_fail(c, e, "launch per-snapshot solve");
   }
   if (timing) cudaEventRecord(c->ev[1], s);

@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(BatchArgs b) {
     bool ok;
     if (q.type == 0) ok = run_instance<OpSSSP>(b, q, i, t, sc, tc, s_stage, s_tile);
     else if (q.type == 1) ok = run_instance<OpSSWP>(b, q, i, t, sc, tc, s_stage, s_tile);
+    else if (q.type == 3) ok = run_instance<OpSSNP>(b, q, i, t, sc, tc, s_stage, s_tile);
     else ok = run_instance<OpBFS>(b, q, i, t, sc, tc, s_stage, s_tile);
     if (rank == 0 && threadIdx.x == 0) {
       b.t_end[i] = global_ns();

@@ -122,6 +122,16 @@ svv_status ensure_instances(svv_ctx* c, uint32_t n) {
 
 }  // namespace
 
+// Teams for batched work: the "batch_teams" knob, else by graph size.  A query
+// on a graph of a few million vertices already fills the GPU in its big rounds,
+// so splitting the grid only pays for smaller graphs (8 teams up to 1M
+// vertices, 2 at 4M, 1 from 8M).
+int default_teams(const svv_ctx* c) {
+  if (c->batch_teams > 0) return c->batch_teams;
+  const uint64_t t = (8ull << 20) / std::max<uint64_t>(c->g.V, 1);
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(8, t));
+}
+
 BatchArgs batch_args(svv_ctx* c) {
   BatchPool& p = c->batch;
   BatchArgs b{};
@@ -146,7 +156,7 @@ BatchArgs batch_args(svv_ctx* c) {
 }
 
 svv_status check_spec(const svv_ctx* c, const svv_query_spec& q) {
-  if ((int)q.type < 0 || (int)q.type > 2) return SVV_EINVAL;
+  if ((int)q.type < 0 || (int)q.type > 3) return SVV_EINVAL;
   if (q.source >= c->g.V || q.win_len == 0 || (uint64_t)q.win_begin + q.win_len > c->g.S || !q.out)
     return SVV_EINVAL;
   return SVV_OK;
@@ -186,7 +196,7 @@ extern "C" svv_status svv_query_batch(svv_ctx* c, uint32_t n, svv_query_spec* sp
   }
   if (inst.empty()) return fail(c, first_bad, "no valid query in the batch");
   const uint32_t m = (uint32_t)inst.size();
-  svv_status st = ensure_pool(c, std::min<int>(c->batch_teams, (int)m), Lmax);
+  svv_status st = ensure_pool(c, std::min<int>(default_teams(c), (int)m), Lmax);
   if (st) return st;
   if ((st = ensure_instances(c, m))) return st;
   BatchPool& p = c->batch;

@@ -47,6 +47,14 @@ struct BatchPool {
   uint64_t ibytes = 0;
 };
 
+// launch knobs of one query type (the autotuner picks them per type)
+struct Knobs {
+  uint32_t solve_cs;
+  int bps;
+  uint32_t relax_lanes;
+  bool skip_same;
+};
+
 // serving: instance ring in host-mapped memory, output arena, live kernel
 struct ServeSlot {
   uint64_t ticket = 0;
@@ -106,6 +114,10 @@ struct svv_ctx {
   bool phase_timing = false;
   bool round_trace = false;
   unsigned long long* trace = nullptr;  // [3][kTraceCap]: intersection, union, relaxation
+  bool skip_same = true;                // per-chunk last-relaxed value (procv)
+  uint32_t relax_lanes = 32;            // lanes per edge in the relaxation (8, 16, 32)
+  uint32_t* procv = nullptr;
+  uint32_t pcap = 0;
   cudaEvent_t ev[7] = {};
 
   // resident graph
@@ -132,10 +144,14 @@ struct svv_ctx {
   uint32_t* staging = nullptr;  // device output for svv_query_host
   uint64_t staging_cap = 0;
 
+  // per-type knobs chosen by svv_autotune
+  svv::Knobs tuned[4] = {};
+  bool has_tuned[4] = {false, false, false, false};
+
   // batched queries
   svv::BatchPool batch;
   svv::ServeState serve;
-  int batch_teams = 8;
+  int batch_teams = 0;  // 0: from the graph size
   int occ_batch = 0;
 
   svv_stats stats{};
@@ -182,6 +198,16 @@ svv_status alloc_n(svv_ctx* c, std::vector<void*>& owner, uint64_t n, T** out) {
 
 inline uint32_t ceil_div(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
 
+// lanes per edge P and snapshots per lane K for a slab of ls snapshots, with
+// at most max_p lanes per edge (P*K is the padded row length)
+inline void slab_shape_p(uint32_t ls, uint32_t max_p, uint32_t& P, uint32_t& K) {
+  uint32_t LP = 8;
+  while (LP < ls) LP <<= 1;
+  P = std::min(LP, max_p);
+  if (LP / P > 8) P = LP / 8;
+  K = LP / P;
+}
+
 inline void slab_shape(uint32_t ls, uint32_t& P, uint32_t& K) {
   if (ls <= 8) {
     P = 8;
@@ -204,6 +230,7 @@ inline void slab_shape(uint32_t ls, uint32_t& P, uint32_t& K) {
 void free_batch(svv_ctx* c);
 void free_serve(svv_ctx* c);
 BatchArgs batch_args(svv_ctx* c);
+int default_teams(const svv_ctx* c);
 svv_status ensure_pool(svv_ctx* c, int want_teams, uint32_t L);
 svv_status status_of(uint32_t qerr, uint32_t done);
 svv_status check_spec(const svv_ctx* c, const svv_query_spec& q);

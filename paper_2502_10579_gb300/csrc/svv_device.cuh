@@ -172,6 +172,16 @@ struct OpBFS {  // CASMIN(Val(v), Val(u) + 1)
   __device__ __forceinline__ static uint32_t atomic(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
 };
 
+struct OpSSNP {  // CASMIN(Val(v), max(Val(u), w))
+  static constexpr uint32_t kIdentity = kInf;
+  static constexpr uint32_t kSource = 0;
+  __device__ __forceinline__ static uint32_t relax(uint32_t sv, uint32_t w) {
+    return sv == kInf ? kInf : (sv > w ? sv : w);
+  }
+  __device__ __forceinline__ static bool better(uint32_t a, uint32_t b) { return a < b; }
+  __device__ __forceinline__ static uint32_t atomic(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
+};
+
 // ---------------------------------------------------------------------------
 // Window predicates on a W-word presence mask (bit i = snapshot i).
 __device__ __forceinline__ uint64_t window_word(Window w, uint32_t j) {

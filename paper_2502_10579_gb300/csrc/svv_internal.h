@@ -79,6 +79,11 @@ struct SolveArgs {
                      // of the frontier's best value (0 = relax every unit)
   unsigned long long* trace;  // optional: per round {frontier units, start ns}
   uint32_t trace_cap;
+  // optional: per work chunk, the source value its edges were last relaxed
+  // with; a chunk whose vertex still holds that value is skipped (relaxing it
+  // again with the same value cannot improve anything).  pcap entries.
+  uint32_t* procv;
+  uint32_t pcap;
 };
 
 struct QrsArgs {

@@ -26,7 +26,7 @@ namespace svv {
 constexpr int kRelaxThreads = 512;
 
 template <class Op, int P, int K>
-__global__ void __launch_bounds__(kRelaxThreads) relax_kernel(RelaxArgs a) {
+__global__ void __launch_bounds__(kRelaxThreads, 3) relax_kernel(RelaxArgs a) {
   __shared__ unsigned long long s_stage[(kRelaxThreads / 32) * kStageUnits];
   const Team t{a.ctl, a.qerr, gridDim.x, blockIdx.x, a.spin_ns};
   relax_team<Op, P, K>(a, t, s_stage);
@@ -35,13 +35,15 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_kernel(RelaxArgs a) {
 // ---------------------------------------------------------------------------
 // Output scatter: out[(s0+i)*V + v] = intersection value if v is stable, else
 // the relaxed value of its row.  A CTA stages a tile of kTV vertices x ls
-// snapshots in shared memory so both the row reads and the snapshot-major
-// writes are coalesced.
+// snapshots in shared memory so the row reads and the snapshot-major writes
+// both coalesce; when V is a multiple of 4 the writes are 16-byte streaming
+// stores (the output is not read again by this query).
 constexpr int kTV = 64;
+constexpr int kTVP = kTV + 4;  // padded tile row: keeps 16-byte alignment
 constexpr int kScatterThreads = 256;
 
 __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(ScatterArgs a) {
-  extern __shared__ uint32_t tile[];  // [ls][kTV + 1]
+  extern __shared__ __align__(16) uint32_t tile[];  // [ls][kTVP]
   if (*a.qerr != 0u) return;
   const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t v0 = blockIdx.x * kTV;
@@ -52,17 +54,26 @@ __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(ScatterArgs a)
     const uint32_t r = a.row[v];
     if (r == kNone) {
       const uint32_t x = a.rI[v];
-      for (uint32_t i = lane; i < a.ls; i += 32u) tile[i * (kTV + 1) + t] = x;
+      for (uint32_t i = lane; i < a.ls; i += 32u) tile[i * kTVP + t] = x;
     } else {
       const uint32_t* src = a.val + ((size_t)r << lps);
-      for (uint32_t i = lane; i < a.ls; i += 32u) tile[i * (kTV + 1) + t] = src[i];
+      for (uint32_t i = lane; i < a.ls; i += 32u) tile[i * kTVP + t] = src[i];
     }
   }
   __syncthreads();
   const uint32_t nv = min((uint32_t)kTV, a.V - v0);
-  for (uint32_t idx = threadIdx.x; idx < a.ls * (uint32_t)kTV; idx += blockDim.x) {
-    const uint32_t i = idx / kTV, t = idx % kTV;
-    if (t < nv) a.out[(size_t)(a.s0 + i) * a.V + v0 + t] = tile[i * (kTV + 1) + t];
+  if ((a.V & 3u) == 0u && nv == (uint32_t)kTV && ((uintptr_t)a.out & 15u) == 0u) {
+    // 16 threads x 16 bytes per tile row, 16 rows per pass
+    const uint32_t q = threadIdx.x & 15u, r0 = threadIdx.x >> 4;
+    for (uint32_t i = r0; i < a.ls; i += kScatterThreads / 16) {
+      const uint4 x = *reinterpret_cast<const uint4*>(tile + i * kTVP + 4 * q);
+      __stcs(reinterpret_cast<uint4*>(a.out + (size_t)(a.s0 + i) * a.V + v0) + q, x);
+    }
+  } else {
+    for (uint32_t idx = threadIdx.x; idx < a.ls * (uint32_t)kTV; idx += blockDim.x) {
+      const uint32_t i = idx / kTV, t = idx % kTV;
+      if (t < nv) a.out[(size_t)(a.s0 + i) * a.V + v0 + t] = tile[i * kTVP + t];
+    }
   }
 }
 
@@ -77,11 +88,20 @@ static cudaError_t launch_r(const RelaxArgs& a, LaunchCfg cfg, cudaStream_t s) {
 
 template <class Op>
 static cudaError_t launch_pk(uint32_t P, uint32_t K, const RelaxArgs& a, LaunchCfg cfg, cudaStream_t s) {
-  if (P == 8) return launch_r<Op, 8, 1>(a, cfg, s);
-  if (P == 16) return launch_r<Op, 16, 1>(a, cfg, s);
-  if (K == 1) return launch_r<Op, 32, 1>(a, cfg, s);
-  if (K == 2) return launch_r<Op, 32, 2>(a, cfg, s);
-  return launch_r<Op, 32, 4>(a, cfg, s);
+  switch (P * 100 + K) {
+    case 801: return launch_r<Op, 8, 1>(a, cfg, s);
+    case 802: return launch_r<Op, 8, 2>(a, cfg, s);
+    case 804: return launch_r<Op, 8, 4>(a, cfg, s);
+    case 808: return launch_r<Op, 8, 8>(a, cfg, s);
+    case 1601: return launch_r<Op, 16, 1>(a, cfg, s);
+    case 1602: return launch_r<Op, 16, 2>(a, cfg, s);
+    case 1604: return launch_r<Op, 16, 4>(a, cfg, s);
+    case 1608: return launch_r<Op, 16, 8>(a, cfg, s);
+    case 3201: return launch_r<Op, 32, 1>(a, cfg, s);
+    case 3202: return launch_r<Op, 32, 2>(a, cfg, s);
+    case 3204: return launch_r<Op, 32, 4>(a, cfg, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_relax(int type, uint32_t P, uint32_t K, const RelaxArgs& a, LaunchCfg cfg,
@@ -89,20 +109,24 @@ cudaError_t launch_relax(int type, uint32_t P, uint32_t K, const RelaxArgs& a, L
   switch (type) {
     case 0: return launch_pk<OpSSSP>(P, K, a, cfg, s);
     case 1: return launch_pk<OpSSWP>(P, K, a, cfg, s);
+    case 3: return launch_pk<OpSSNP>(P, K, a, cfg, s);
     default: return launch_pk<OpBFS>(P, K, a, cfg, s);
   }
 }
 
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
   const uint32_t blocks = (a.V + kTV - 1) / kTV;
-  const size_t smem = (size_t)a.ls * (kTV + 1) * sizeof(uint32_t);
+  const size_t smem = (size_t)a.ls * kTVP * sizeof(uint32_t);
   scatter_kernel<<<blocks, kScatterThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <class Op>
 static int occ_op(int threads) {
-  const void* ks[] = {(const void*)relax_kernel<Op, 8, 1>, (const void*)relax_kernel<Op, 16, 1>,
+  const void* ks[] = {(const void*)relax_kernel<Op, 8, 1>,  (const void*)relax_kernel<Op, 8, 2>,
+                      (const void*)relax_kernel<Op, 8, 4>,  (const void*)relax_kernel<Op, 8, 8>,
+                      (const void*)relax_kernel<Op, 16, 1>, (const void*)relax_kernel<Op, 16, 2>,
+                      (const void*)relax_kernel<Op, 16, 4>, (const void*)relax_kernel<Op, 16, 8>,
                       (const void*)relax_kernel<Op, 32, 1>, (const void*)relax_kernel<Op, 32, 2>,
                       (const void*)relax_kernel<Op, 32, 4>};
   int best = 1 << 30;
@@ -116,8 +140,10 @@ static int occ_op(int threads) {
 
 int occupancy_relax(int threads) {
   int a = occ_op<OpSSSP>(threads), b = occ_op<OpSSWP>(threads), c = occ_op<OpBFS>(threads);
+  int d = occ_op<OpSSNP>(threads);
   int m = a < b ? a : b;
-  return m < c ? m : c;
+  m = m < c ? m : c;
+  return m < d ? m : d;
 }
 
 }  // namespace svv

@@ -31,45 +31,67 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
   if (!t.sync()) return false;
   if (a.trace && gtid == 0 && a.trace_cap) a.trace[0] = global_ns() & 0xFFFFFFFFFFull;
 
-  // ---- round 0b: seed from addition edges with an unstable sink
+  // ---- round 0b: seed from addition edges with an unstable sink; two
+  // qualifying edges per warp iteration, lanes over the slab's snapshots
   for (uint32_t k0 = gwarp * 32u; k0 < g.NF; k0 += nwarps * 32u) {
     const uint32_t k = k0 + lane;
     bool qual = false;
+    uint32_t rx = kNone, cand = 0;
     if (k < g.NF) {
-      const uint32_t rx = a.row[__ldg(&g.nfcw[k].x)];
+      const uint2 e = __ldg(g.nfcw + k);
+      rx = a.row[e.x];
       if (rx != kNone) {
         bool any, all;
         window_any_all(g.nfmask + (size_t)k * g.W, a.win, any, all);
         qual = any && !all;
+        if (qual) cand = Op::relax(a.rI[__ldg(g.nfsrc + k)], e.y);
       }
     }
     unsigned bq = __ballot_sync(kFullMask, qual);
     while (bq) {
-      const uint32_t kj = k0 + (__ffs(bq) - 1);
+      int j[2];
+      j[0] = __ffs(bq) - 1;
       bq &= bq - 1u;
-      const uint2 e = __ldg(g.nfcw + kj);
-      const uint32_t rx = a.row[e.x];
-      const uint32_t cand = Op::relax(a.rI[__ldg(g.nfsrc + kj)], e.y);
-      const uint64_t* m = g.nfmask + (size_t)kj * g.W;
-      bool imp = false;
+      j[1] = bq ? __ffs(bq) - 1 : -1;
+      if (bq) bq &= bq - 1u;
+      uint32_t ex[2], ec[2];
+      const uint64_t* em[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int src = j[h] < 0 ? j[0] : j[h];
+        ex[h] = __shfl_sync(kFullMask, rx, src);
+        ec[h] = __shfl_sync(kFullMask, cand, src);
+        em[h] = g.nfmask + (size_t)(k0 + src) * g.W;
+      }
+      bool imp[2] = {false, false};
       for (uint32_t i = lane; i < a.ls; i += 32u) {
-        if (mask_bit(m, snap0 + i)) {
-          uint32_t* p = a.val + ((size_t)rx << lps) + i;
-          if (Op::better(cand, ld_cg(p))) {
-            const uint32_t old = Op::atomic(p, cand);
-            imp |= Op::better(cand, old);
+        bool want[2];
+        uint32_t curv[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          want[h] = j[h] >= 0 && mask_bit(em[h], snap0 + i);
+          curv[h] = want[h] ? ld_cg(a.val + ((size_t)ex[h] << lps) + i) : 0u;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (want[h] && Op::better(ec[h], curv[h])) {
+            const uint32_t old = Op::atomic(a.val + ((size_t)ex[h] << lps) + i, ec[h]);
+            imp[h] |= Op::better(ec[h], old);
           }
         }
       }
-      const bool any_imp = __any_sync(kFullMask, imp);
-      bool push = false;
-      uint32_t deg = 0;
-      if (any_imp && lane == 0 && atomicExch(a.stamp + rx, 1u) != 1u) {
-        push = true;
-        const uint4 d = a.qrow[rx];
-        deg = d.w - d.x;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool any_imp = __any_sync(kFullMask, imp[h]);
+        bool push = false;
+        uint32_t deg = 0;
+        if (any_imp && lane == 0 && atomicExch(a.stamp + ex[h], 1u) != 1u) {
+          push = true;
+          const uint4 d = a.qrow[ex[h]];
+          deg = d.w - d.x;
+        }
+        stage_push_units(push, ex[h], deg, a.cshift, st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
       }
-      stage_push_units(push, rx, deg, a.cshift, st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
     }
   }
   stage_flush_cta(st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
@@ -140,14 +162,15 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
         bool pend = false;
         uint32_t pend_x = 0;
         const uint32_t nj = min((uint32_t)P, maxcnt - j0);
-        // two edges per iteration: both target rows are loaded before either
-        // is compared, so each lane keeps two load chains in flight
-        for (uint32_t jj = 0; jj < nj; jj += 2u) {
-          uint32_t ex[2], ewt[2];
-          uint64_t em0[2], em1[2];
-          bool ev[2];
+        // H edges per iteration: every target row is loaded before any is
+        // compared, so each lane keeps H load chains in flight
+        constexpr int H = (K <= 2) ? 4 : 2;
+        for (uint32_t jj = 0; jj < nj; jj += H) {
+          uint32_t ex[H], ewt[H];
+          uint64_t em0[H], em1[H];
+          bool ev[H];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < H; ++h) {
             const uint32_t src = min(jj + h, (uint32_t)P - 1u);
             ex[h] = __shfl_sync(kFullMask, xr, src, P);
             ewt[h] = __shfl_sync(kFullMask, w, src, P);
@@ -156,10 +179,10 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
             if (P * K > 64) em1[h] = __shfl_sync(kFullMask, m1, src, P);
             ev[h] = (jj + h < nj) && (beg + j0 + jj + h) < end;
           }
-          uint32_t curv[2][K];
-          bool want[2][K];
+          uint32_t curv[H][K];
+          bool want[H][K];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < H; ++h) {
             uint32_t* row = a.val + ((size_t)ex[h] << lps) + gl;
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) {
@@ -169,9 +192,10 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
               curv[h][kk] = want[h][kk] ? ld_cg(row + kk * P) : 0u;
             }
           }
-          bool imp[2] = {false, false};
+          bool imp[H];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < H; ++h) {
+            imp[h] = false;
             uint32_t* row = a.val + ((size_t)ex[h] << lps) + gl;
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) {
@@ -185,7 +209,7 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
             }
           }
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < H; ++h) {
             const unsigned bi = __ballot_sync(kFullMask, imp[h]) & gmask;
             if (gl == jj + h && bi) {
               pend = true;

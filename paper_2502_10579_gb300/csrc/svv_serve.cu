@@ -158,7 +158,7 @@ svv_status svv_serve_start(svv_ctx* c, uint32_t max_window, uint32_t capacity, u
   if (max_window == 0 || max_window > c->g.S) return fail(c, SVV_EINVAL, "max_window must be in [1, S]");
   if (capacity == 0 || capacity > (1u << 24)) return fail(c, SVV_EINVAL, "capacity must be in [1, 2^24]");
   DeviceGuard dg(c->device);
-  svv_status st = ensure_pool(c, c->batch_teams, max_window);
+  svv_status st = ensure_pool(c, default_teams(c), max_window);
   if (st) return st;
   ServeState& v = c->serve;
   v.cap = capacity;

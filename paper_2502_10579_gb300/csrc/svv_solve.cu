@@ -21,7 +21,7 @@ namespace svv {
 constexpr int kSolveThreads = 512;
 
 template <class Op, int PRED>
-__global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs a) {
+__global__ void __launch_bounds__(kSolveThreads, 3) solve_kernel(SolveArgs a) {
   __shared__ unsigned long long s_stage[(kSolveThreads / 32) * kStageUnits];
   const Team t{a.ctl, a.qerr, gridDim.x, blockIdx.x, a.spin_ns};
   solve_team<Op, PRED>(a, t, s_stage);
@@ -48,6 +48,7 @@ cudaError_t launch_solve(int type, int pred, const SolveArgs& a, LaunchCfg cfg, 
   switch (type) {
     case 0: return launch_pred<OpSSSP>(pred, a, cfg, s);
     case 1: return launch_pred<OpSSWP>(pred, a, cfg, s);
+    case 3: return launch_pred<OpSSNP>(pred, a, cfg, s);
     default: return launch_pred<OpBFS>(pred, a, cfg, s);
   }
 }
@@ -59,7 +60,8 @@ int occupancy_solve(int threads) {
       (const void*)solve_kernel<OpSSSP, kPredBit>, (const void*)solve_kernel<OpSSWP, kPredAll>,
       (const void*)solve_kernel<OpSSWP, kPredAny>, (const void*)solve_kernel<OpSSWP, kPredBit>,
       (const void*)solve_kernel<OpBFS, kPredAll>,  (const void*)solve_kernel<OpBFS, kPredAny>,
-      (const void*)solve_kernel<OpBFS, kPredBit>};
+      (const void*)solve_kernel<OpBFS, kPredBit>,  (const void*)solve_kernel<OpSSNP, kPredAll>,
+      (const void*)solve_kernel<OpSSNP, kPredAny>, (const void*)solve_kernel<OpSSNP, kPredBit>};
   for (const void* k : ks) {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, 0) != cudaSuccess) return 0;

@@ -38,6 +38,9 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
       a.stamp[v] = 0u;
     }
   }
+  // no chunk has been relaxed yet: the identity is never a queued value
+  if (a.procv)
+    for (uint32_t k = gtid; k < a.pcap; k += nthreads) a.procv[k] = Op::kIdentity;
   if (!t.sync()) return false;
   if (a.trace && gtid == 0 && a.trace_cap) a.trace[0] = global_ns() & 0xFFFFFFFFFFull;
 
@@ -142,6 +145,12 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
         if (PRED == kPredAll && a.skip_nf) end = min(end, fe);
         cnt = end > beg ? end - beg : 0u;
         sv = ld_cg(a.val + v);
+        if (a.procv && cnt) {
+          // chunk ids v + rp[v]/C + ch are distinct across vertices
+          uint32_t* pv = a.procv + v + (r0 >> a.cshift) + ch;
+          if (ld_cg(pv) == sv) cnt = 0;
+          else *pv = sv;
+        }
         if (far_on && (Op::better(0u, 1u) ? sv > bound : sv < bound)) {
           // far: queue all of v's units again, once per round (stamp), and
           // skip this one now

@@ -12,7 +12,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-SVV_SSSP, SVV_SSWP, SVV_BFS = 0, 1, 2
+SVV_SSSP, SVV_SSWP, SVV_BFS, SVV_SSNP = 0, 1, 2, 3
 STATUS = {0: "SVV_OK", 1: "SVV_EINVAL", 2: "SVV_ENOMEM", 3: "SVV_ECUDA", 4: "SVV_ETIMEOUT",
           5: "SVV_EBUSY", 6: "SVV_ENOTLOADED", 7: "SVV_EINTERNAL"}
 
@@ -24,7 +24,7 @@ EXPORTS = ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "sv
            "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats", "svv_device_bytes", "svv_status_str",
            "svv_last_error", "svv_destroy", "svv_solve_snapshot_noalloc",
            "svv_get_round_trace", "svv_query_batch", "svv_serve_start", "svv_submit", "svv_poll",
-           "svv_ticket_info", "svv_release", "svv_serve_stop", "svv_serve_replay")
+           "svv_ticket_info", "svv_release", "svv_serve_stop", "svv_serve_replay", "svv_autotune")
 
 
 class SvvError(RuntimeError):
@@ -36,6 +36,12 @@ class SvvError(RuntimeError):
 class svv_query_spec(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("source", ctypes.c_uint32), ("win_begin", ctypes.c_uint32),
                 ("win_len", ctypes.c_uint32), ("out", ctypes.c_void_p), ("status", ctypes.c_int)]
+
+
+class svv_tune_result(ctypes.Structure):
+    _fields_ = [("solve_chunk", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("relax_lanes", ctypes.c_uint32), ("skip_same", ctypes.c_uint32),
+                ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float), ("candidates", ctypes.c_uint32)]
 
 
 class svv_stats(ctypes.Structure):
@@ -93,6 +99,8 @@ def lib():
     L.svv_release.argtypes = [P, u64]
     L.svv_serve_stop.argtypes = [P]
     L.svv_serve_replay.argtypes = [P, u32, ctypes.POINTER(svv_query_spec), P, P, P]
+    L.svv_autotune.argtypes = [P, i32, u32, u32, u32, u32, ctypes.POINTER(svv_tune_result)]
+    L.svv_autotune.restype = i32
     for f in ("svv_serve_start", "svv_submit", "svv_poll", "svv_ticket_info", "svv_release", "svv_serve_stop",
               "svv_serve_replay"):
         getattr(L, f).restype = i32
@@ -218,6 +226,13 @@ def svv_query_batch(ctx, specs, stream=None):
     if st != 0 and all(x != 0 for x in statuses):
         _check(ctx, st)
     return statuses
+
+
+def svv_autotune(ctx, qtype: int, source: int, win_begin: int, win_len: int, reps: int = 3) -> dict:
+    r = svv_tune_result()
+    _check(ctx, lib().svv_autotune(ctx, qtype, source, win_begin, win_len, reps, ctypes.byref(r)))
+    return {name: (float(getattr(r, name)) if name.endswith("_ms") else int(getattr(r, name)))
+            for name, _ in svv_tune_result._fields_}
 
 
 def svv_serve_start(ctx, max_window: int, capacity: int = 4096, arena_bytes: int = 0):

@@ -26,7 +26,7 @@ def _mixed(log, n, seed, l_lo=1, l_hi=None):
     for k in range(n):
         L = int(rng.integers(l_lo, l_hi + 1))
         b = int(rng.integers(0, log.S - L + 1))
-        out.append((k % 3, int(rng.integers(0, log.V)), b, L))
+        out.append((k % 4, int(rng.integers(0, log.V)), b, L))
     return out
 
 

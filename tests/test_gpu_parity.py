@@ -16,7 +16,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 INF = 0xFFFFFFFF
-TYPES = (0, 1, 2)
+TYPES = (0, 1, 2, 3)
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
@@ -89,7 +89,7 @@ def test_golden_vertex_c(svv):
                                                    np.array(g["w"], np.uint32), t_add, t_del)
     with svv.Context(0) as ctx:
         ctx.load_csr(g["V"], g["S"], rp, col, w, mask)
-        for name, t in (("sssp", 0), ("sswp", 1), ("bfs", 2)):
+        for name, t in (("sssp", 0), ("sswp", 1), ("bfs", 2), ("ssnp", 3)):
             exp = g["expected"][name]
             got = _iu(svv, ctx, t, g["source"], 0, 2)
             np.testing.assert_array_equal(got, np.array(exp["snapshots"], np.uint32))
@@ -153,7 +153,7 @@ def test_degenerate_graphs(svv):
         # one vertex, no edges
         ctx.load_csr(1, 3, np.zeros(2, np.uint64), np.zeros(0, np.uint32), np.zeros(0, np.uint32),
                      np.zeros(0, np.uint64))
-        for t, v in ((0, 0), (1, INF), (2, 0)):
+        for t, v in ((0, 0), (1, INF), (2, 0), (3, 0)):
             assert _iu(svv, ctx, t, 0, 0, 3).tolist() == [[v]] * 3
         # edges present in no snapshot are dropped; self-loops and multi-edges kept
         rp = np.array([0, 3, 4, 4], np.uint64)
@@ -193,7 +193,7 @@ def test_inputs_on_device_and_host_output(svv, small):
 def test_error_paths(svv, small):
     log, ctx = small
     out = ctx.empty_out(8)
-    for args in [(3, 0, 0, 1), (0, log.V, 0, 1), (0, 0, 0, 0), (0, 0, 5, 4)]:
+    for args in [(4, 0, 0, 1), (0, log.V, 0, 1), (0, 0, 0, 0), (0, 0, 5, 4)]:
         with pytest.raises(svv.SvvError) as e:
             svv.svv_query(ctx.h, *args, out)
         assert e.value.status == 1

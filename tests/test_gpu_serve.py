@@ -27,7 +27,7 @@ def _requests(log, n, seed, l_hi):
     out = []
     for k in range(n):
         L = int(rng.integers(1, l_hi + 1))
-        out.append((int(rng.integers(0, 3)), int(rng.integers(0, log.V)), int(rng.integers(0, log.S - L + 1)), L))
+        out.append((int(rng.integers(0, 4)), int(rng.integers(0, log.V)), int(rng.integers(0, log.S - L + 1)), L))
     return out
 
 

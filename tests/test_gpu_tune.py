@@ -1,0 +1,25 @@
+"""Autotuner: picks per-type knobs by timing a probe query; results stay exact."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_keeps_results_exact():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_10579_gb300 import svv
+    log = W.scaled_rmat(scale=14, edge_factor=8, n_snapshots=32, rate=0.002, seed=21)
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        for t in (0, 2):
+            r = svv.svv_autotune(ctx.h, t, 0, 0, log.S, reps=2)
+            assert r["candidates"] >= 2
+            assert r["solve_chunk"] in (32, 64) and r["relax_lanes"] in (16, 32)
+            assert 0 < r["best_ms"] <= r["default_ms"]
+            for b, L in [(0, log.S), (5, 9)]:
+                np.testing.assert_array_equal(svv.to_u32(ctx.query(t, 3, b, L)), oracle.query(log, t, 3, b, L))
