@@ -279,6 +279,10 @@ svv_status svv_autotune(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t w
  * (near-far width of the SSSP / SSWP solves: a frontier round relaxes only the
  * vertices within this distance of the round's best value and keeps the rest
  * queued; 0 relaxes every queued vertex; results are identical either way),
+ * "graph" (1 = svv_query captures its launches into a CUDA graph, updates the
+ * instantiated graph in place for the next query of the same shape and
+ * replays it; falls back to direct launches where capture is refused; phase
+ * timing is not recorded in this mode),
  * "batch_teams" (teams of svv_query_batch and the server, 1..64; 0 = by graph
  * size: 8 up to 1M vertices, fewer above, 1 from 8M), "relax_lanes" (8, 16, 32:
  * lanes per edge in the relaxation), "skip_same" (1 = skip work chunks already

@@ -199,6 +199,8 @@ void svv_destroy(svv_ctx* c) {
     for (auto& e : c->ev)
       if (e) cudaEventDestroy(e);
     if (c->trace) cudaFree(c->trace);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   }
   delete c;
 }
@@ -234,6 +236,9 @@ svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
         if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
     }
     c->phase_timing = v != 0;
+  } else if (k == "graph") {
+    if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "graph is 0 or 1");
+    c->graph_mode = v != 0;
   } else if (k == "relax_lanes") {
     if (v != 8 && v != 16 && v != 32) return fail(c, SVV_EINVAL, "relax_lanes is 8, 16 or 32");
     c->relax_lanes = (uint32_t)v;
@@ -435,18 +440,17 @@ svv_status svv_load(svv_ctx* c, uint32_t V, uint64_t E, uint32_t S, const uint64
   return SVV_OK;
 }
 
-svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, uint32_t wl, uint32_t* out,
-                     void* stream) {
-  svv_status st = check_query(c, (int)type, source, wb, wl, out);
-  if (st) return st;
-  DeviceGuard dg(c->device);
-  if ((st = ensure_window(c, wl))) return st;
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// Enqueue every step of one query on stream s (no host synchronisation, so a
+// graph capture can record it).  With timing, CUDA events bracket the phases.
+svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32_t wl, uint32_t* out,
+                         cudaStream_t s, bool timing, float* ms_relax_out, float* ms_scatter_out) {
   cudaError_t e = cudaMemsetAsync(c->ctl, 0, sizeof(TeamCtl) * 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->qerr, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "memset");
-  const int t = (int)type;
-  const bool timing = c->phase_timing;
   if (timing) cudaEventRecord(c->ev[0], s);
 
   // a1: intersection graph (edges present in every window snapshot)
@@ -570,6 +574,82 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
       }
     }
   }
+  *ms_relax_out = ms_relax;
+  *ms_scatter_out = ms_scatter;
+  return SVV_OK;
+}
+
+// Graph mode: capture the query's launches, update the instantiated graph in
+// place (same topology for the same window shape) or instantiate it, launch it.
+svv_status graph_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32_t wl, uint32_t* out,
+                       cudaStream_t s, bool* captured) {
+  *captured = false;
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return SVV_ECUDA;
+  }
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return SVV_ECUDA;
+  }
+  float a = 0.f, b = 0.f;
+  svv_status st = enqueue_query(c, t, source, wb, wl, out, c->cap_stream, false, &a, &b);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (st || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st ? st : SVV_ECUDA;
+  }
+  bool ok = false;
+  if (c->gexec) {
+    cudaGraphExecUpdateResultInfo info;
+    ok = cudaGraphExecUpdate(c->gexec, g, &info) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+  }
+  if (!ok) {
+    if (cudaGraphInstantiate(&c->gexec, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      c->gexec = nullptr;
+      cudaGraphDestroy(g);
+      return SVV_ECUDA;
+    }
+    c->graph_builds++;
+  }
+  cudaGraphDestroy(g);
+  *captured = true;
+  if ((e = cudaGraphLaunch(c->gexec, s)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+  c->graph_launches++;
+  return SVV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, uint32_t wl, uint32_t* out,
+                     void* stream) {
+  svv_status st = check_query(c, (int)type, source, wb, wl, out);
+  if (st) return st;
+  DeviceGuard dg(c->device);
+  if ((st = ensure_window(c, wl))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int t = (int)type;
+  bool timing = c->phase_timing;
+  float ms_relax = 0.f, ms_scatter = 0.f;
+  bool done = false;
+  if (c->graph_mode && !c->round_trace) {
+    bool captured = false;
+    st = graph_query(c, t, source, wb, wl, out, s, &captured);
+    if (captured && st) return st;
+    done = captured;
+    if (done) timing = false;
+  }
+  if (!done && (st = enqueue_query(c, t, source, wb, wl, out, s, timing, &ms_relax, &ms_scatter))) return st;
   st = finish(c, s, 4);
   svv_stats& S = c->stats;
   S = svv_stats{};

@@ -144,6 +144,12 @@ struct svv_ctx {
   uint32_t* staging = nullptr;  // device output for svv_query_host
   uint64_t staging_cap = 0;
 
+  // graph mode: each query's launches captured and replayed as one graph
+  bool graph_mode = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  uint64_t graph_builds = 0, graph_launches = 0;
+
   // per-type knobs chosen by svv_autotune
   svv::Knobs tuned[4] = {};
   bool has_tuned[4] = {false, false, false, false};
