@@ -198,6 +198,19 @@ svv_status svv_serve_replay(svv_ctx *ctx, uint32_t n, const svv_query_spec *spec
 /* Stop the server (pending requests are abandoned) and free its memory. */
 svv_status svv_serve_stop(svv_ctx *ctx);
 
+/* svv_query without the dense output (the paper keeps one result array per
+ * snapshot; this returns what determines them): cap_out[v] = the value of v
+ * on the window's intersection graph, row_out[v] = v's row or 0xFFFFFFFF if v
+ * is stable, rows_out[r*win_len + i] = the value of the vertex of row r in
+ * snapshot win_begin+i.  So value(v, i) = row_out[v] == 0xFFFFFFFF ?
+ * cap_out[v] : rows_out[row_out[v]*win_len + i].  All three are caller DEVICE
+ * buffers (V, V and rows_cap uint32); *unstable_out (host, may be NULL)
+ * receives the number of rows U.  SVV_ENOMEM if rows_cap < U*win_len. */
+svv_status svv_query_compact(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
+                             uint32_t win_len, uint32_t *cap_out, uint32_t *row_out,
+                             uint32_t *rows_out, uint64_t rows_cap, uint32_t *unstable_out,
+                             void *cuda_stream);
+
 /* The same query answered the plain way (Fig. 2a): one full solve per window
  * snapshot, each written straight into its row of `out`.  Same arguments and
  * output as svv_query; on failure the rows of `out` are unspecified. */
@@ -279,6 +292,11 @@ svv_status svv_autotune(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t w
  * (near-far width of the SSSP / SSWP solves: a frontier round relaxes only the
  * vertices within this distance of the round's best value and keeps the rest
  * queued; 0 relaxes every queued vertex; results are identical either way),
+ * "slab_max" (1..128, default 128: snapshots relaxed per pass; 1 evaluates
+ * the snapshots one after another over the subgraph, the paper's
+ * non-concurrent mode), "prune" (1 default; 0 gives every vertex a row and
+ * keeps every edge -- common-graph direct-hop evaluation without the
+ * stable-vertex pruning; results are identical),
  * "graph" (1 = svv_query captures its launches into a CUDA graph, updates the
  * instantiated graph in place for the next query of the same shape and
  * replays it; falls back to direct launches where capture is refused; phase

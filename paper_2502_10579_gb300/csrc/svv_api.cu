@@ -47,7 +47,7 @@ svv_status ensure_window(svv_ctx* c, uint32_t L) {
   const uint32_t QW = ceil_div(L, 64);
   const uint64_t need_m = (uint64_t)std::max<uint32_t>(c->g.NF, 1) * QW;
   uint32_t P, K;
-  slab_shape(std::min(L, kMaxSlab), P, K);
+  slab_shape(std::min(L, c->slab_max), P, K);
   const uint64_t need_v = (uint64_t)std::max<uint32_t>(c->g.V, 1) * P * K;
   if (need_m > c->mcap) {
     if (c->qmask) {
@@ -118,6 +118,7 @@ svv_status finish(svv_ctx* c, cudaStream_t s, int nctl_copy) {
   if (e != cudaSuccess) return cuda_fail(c, e, "query");
   const uint32_t q = *c->hqerr;
   if (q == kErrTimeout) return fail(c, SVV_ETIMEOUT, "a device wait or the round cap expired");
+  if (q == 2u) return fail(c, SVV_ENOMEM, "rows_out is smaller than U * win_len");
   if (q != 0) return fail(c, SVV_EINTERNAL, "device capacity check failed");
   c->err.clear();
   return SVV_OK;
@@ -236,6 +237,12 @@ svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
         if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
     }
     c->phase_timing = v != 0;
+  } else if (k == "slab_max") {
+    if (v < 1 || v > (int64_t)kMaxSlab) return fail(c, SVV_EINVAL, "slab_max in [1, 128]");
+    c->slab_max = (uint32_t)v;
+  } else if (k == "prune") {
+    if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "prune is 0 or 1");
+    c->prune = v != 0;
   } else if (k == "graph") {
     if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "graph is 0 or 1");
     c->graph_mode = v != 0;
@@ -446,8 +453,18 @@ namespace {
 
 // Enqueue every step of one query on stream s (no host synchronisation, so a
 // graph capture can record it).  With timing, CUDA events bracket the phases.
+// With rows_out set, the scatter is replaced by a copy of the relaxed rows
+// (compact output).
+struct CompactOut {
+  uint32_t* cap_out;
+  uint32_t* row_out;
+  uint32_t* rows_out;
+  uint64_t rows_cap;
+};
+
 svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32_t wl, uint32_t* out,
-                         cudaStream_t s, bool timing, float* ms_relax_out, float* ms_scatter_out) {
+                         cudaStream_t s, bool timing, float* ms_relax_out, float* ms_scatter_out,
+                         const CompactOut* co = nullptr) {
   cudaError_t e = cudaMemsetAsync(c->ctl, 0, sizeof(TeamCtl) * 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->qerr, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "memset");
@@ -480,7 +497,7 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
     a2.trace = c->trace + kTraceCap;
     a2.trace_cap = kTraceCap;
   }
-  if ((e = launch_solve(t, kPredAny, a2, cfg_for(c, c->occ_solve, kn.bps), s)) != cudaSuccess)
+  if (c->prune && (e = launch_solve(t, kPredAny, a2, cfg_for(c, c->occ_solve, kn.bps), s)) != cudaSuccess)
     return cuda_fail(c, e, "launch union solve");
   if (timing) cudaEventRecord(c->ev[2], s);
   // a3+a4: stable compaction and the Q-relevant subgraph
@@ -488,6 +505,7 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
   q.g = c->g;
   q.win = Window{wb, wl};
   q.QW = ceil_div(wl, 64);
+  q.prune = c->prune ? 1 : 0;
   q.rI = c->rI;
   q.rU = c->rU;
   q.row = c->row;
@@ -513,8 +531,9 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
   float ms_relax = 0.f, ms_scatter = 0.f;
   // a5+a6 per slab of at most 128 snapshots (a window longer than that is
   // relaxed slab by slab over the same subgraph; snapshots are independent)
-  for (uint32_t s0 = 0; s0 < wl; s0 += kMaxSlab) {
-    const uint32_t ls = std::min(kMaxSlab, wl - s0);
+  const uint32_t slab = std::max<uint32_t>(1, std::min(c->slab_max, kMaxSlab));
+  for (uint32_t s0 = 0; s0 < wl; s0 += slab) {
+    const uint32_t ls = std::min(slab, wl - s0);
     uint32_t P, K;
     slab_shape_p(ls, kn.relax_lanes, P, K);
     if (s0 > 0 && (e = cudaMemsetAsync(c->ctl + 3, 0, sizeof(TeamCtl), s)) != cudaSuccess)
@@ -551,6 +570,21 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
     if ((e = launch_relax(t, P, K, r, cfg_for(c, c->occ_relax, kn.bps), s)) != cudaSuccess)
       return cuda_fail(c, e, "launch relaxation");
     if (timing) cudaEventRecord(c->ev[4], s);
+    if (co) {
+      CompactArgs ca{};
+      ca.counts = &(c->ctl + 2)->aux[0];
+      ca.val = c->val;
+      ca.LP = P * K;
+      ca.s0 = s0;
+      ca.ls = ls;
+      ca.wl = wl;
+      ca.rows_out = co->rows_out;
+      ca.rows_cap = co->rows_cap;
+      ca.qerr = c->qerr;
+      if ((e = launch_compact(ca, s)) != cudaSuccess) return cuda_fail(c, e, "launch compact copy");
+      if (timing) cudaEventRecord(c->ev[5], s);
+      continue;
+    }
     ScatterArgs sa{};
     sa.V = c->g.V;
     sa.s0 = s0;
@@ -564,7 +598,7 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
     if ((e = launch_scatter(sa, s)) != cudaSuccess) return cuda_fail(c, e, "launch scatter");
     if (timing) {
       cudaEventRecord(c->ev[5], s);
-      if (wl > kMaxSlab) {  // several slabs: accumulate per slab
+      if (wl > slab) {  // several slabs: accumulate per slab
         float a = 0.f, b = 0.f;
         cudaEventSynchronize(c->ev[5]);
         cudaEventElapsedTime(&a, c->ev[6], c->ev[4]);
@@ -573,6 +607,13 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
         ms_scatter += b;
       }
     }
+  }
+  if (co) {
+    const size_t n = (size_t)c->g.V * sizeof(uint32_t);
+    if (co->cap_out && (e = cudaMemcpyAsync(co->cap_out, c->rI, n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return cuda_fail(c, e, "copy intersection values");
+    if (co->row_out && (e = cudaMemcpyAsync(co->row_out, c->row, n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return cuda_fail(c, e, "copy row map");
   }
   *ms_relax_out = ms_relax;
   *ms_scatter_out = ms_scatter;
@@ -667,7 +708,7 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
     cudaEventElapsedTime(&S.ms_cap, c->ev[0], c->ev[1]);
     cudaEventElapsedTime(&S.ms_cup, c->ev[1], c->ev[2]);
     cudaEventElapsedTime(&S.ms_qrs, c->ev[2], c->ev[3]);
-    if (wl > kMaxSlab) {
+    if (wl > std::max<uint32_t>(1, std::min(c->slab_max, kMaxSlab))) {
       S.ms_relax = ms_relax;
       S.ms_scatter = ms_scatter;
     } else {
@@ -675,6 +716,27 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
       cudaEventElapsedTime(&S.ms_scatter, c->ev[4], c->ev[5]);
     }
   }
+  return st;
+}
+
+svv_status svv_query_compact(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, uint32_t wl,
+                             uint32_t* cap_out, uint32_t* row_out, uint32_t* rows_out, uint64_t rows_cap,
+                             uint32_t* unstable_out, void* stream) {
+  svv_status st = check_query(c, (int)type, source, wb, wl, rows_out);
+  if (st) return st;
+  if (!cap_out || !row_out) return fail(c, SVV_EINVAL, "cap_out and row_out are required");
+  DeviceGuard dg(c->device);
+  if ((st = ensure_window(c, wl))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const CompactOut co{cap_out, row_out, rows_out, rows_cap};
+  float a = 0.f, b = 0.f;
+  if ((st = enqueue_query(c, (int)type, source, wb, wl, nullptr, s, false, &a, &b, &co))) return st;
+  st = finish(c, s, 4);
+  c->stats = svv_stats{};
+  c->stats.unstable = c->hctl[2].aux[0];
+  c->stats.qrs_edges = c->hctl[2].aux[2];
+  c->stats.qrs_masked = c->hctl[2].aux[3];
+  if (unstable_out) *unstable_out = c->hctl[2].aux[0];
   return st;
 }
 

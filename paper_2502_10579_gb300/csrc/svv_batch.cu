@@ -106,6 +106,7 @@ __device__ bool run_instance(const BatchArgs& b, const BatchInstance& q, uint32_
   r.g = b.g;
   r.win = Window{q.wb, q.wl};
   r.QW = (q.wl + 63u) / 64u;
+  r.prune = 1;
   r.rI = sc.rI;
   r.rU = sc.rU;
   r.row = sc.row;

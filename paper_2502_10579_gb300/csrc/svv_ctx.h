@@ -144,6 +144,12 @@ struct svv_ctx {
   uint32_t* staging = nullptr;  // device output for svv_query_host
   uint64_t staging_cap = 0;
 
+  // paper's ablations (Table 3): snapshots per relaxation pass (1 = one
+  // snapshot at a time, the non-concurrent mode) and stable-vertex pruning
+  // (off = every vertex relaxed, the common-graph direct-hop evaluation)
+  uint32_t slab_max = svv::kMaxSlab;
+  bool prune = true;
+
   // graph mode: each query's launches captured and replayed as one graph
   bool graph_mode = false;
   cudaStream_t cap_stream = nullptr;

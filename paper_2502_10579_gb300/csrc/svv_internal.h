@@ -90,6 +90,8 @@ struct QrsArgs {
   DevGraph g;
   Window win;
   uint32_t QW;            // mask words per relaxation edge: ceil(win.l / 64)
+  int prune;              // 1: only vertices whose bounds differ get rows (the
+                          // method); 0: every vertex does (no pruning)
   const uint32_t* rI;     // intersection-graph values
   const uint32_t* rU;     // union-graph values
   uint32_t* row;          // [V] vertex -> row, kNone if stable
@@ -136,6 +138,19 @@ struct RelaxArgs {
   unsigned long long* trace;
   uint32_t trace_cap;
 };
+
+// compact output: the relaxed rows of one slab copied to the caller's U x wl
+// array (row-major, stride wl)
+struct CompactArgs {
+  const unsigned int* counts;  // U at [0]
+  const uint32_t* val;
+  uint32_t LP, s0, ls, wl;
+  uint32_t* rows_out;
+  unsigned long long rows_cap;  // entries
+  uint32_t* qerr;
+};
+
+cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 
 struct ScatterArgs {
   uint32_t V;

@@ -179,7 +179,7 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
   {
     uint32_t cnt = 0, nun = 0, z0 = 0, z1 = 0;
     for (uint32_t v = lo + tid; v < hi; v += blockDim.x) {
-      if (a.rI[v] != a.rU[v]) {
+      if (!a.prune || a.rI[v] != a.rU[v]) {
         ++cnt;
         nun += (__ldg(g.rp + v + 1) - __ldg(g.rp + v) + C - 1u) >> a.cshift;
       }
@@ -219,7 +219,7 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
     for (uint32_t base = lo; base < hi; base += blockDim.x) {
       const uint32_t v = base + tid;
       uint32_t flag = 0, nu = 0;
-      if (v < hi && a.rI[v] != a.rU[v]) {
+      if (v < hi && (!a.prune || a.rI[v] != a.rU[v])) {
         flag = 1;
         nu = (__ldg(g.rp + v + 1) - __ldg(g.rp + v) + C - 1u) >> a.cshift;
       }

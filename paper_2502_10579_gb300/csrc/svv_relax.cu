@@ -77,6 +77,29 @@ __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(ScatterArgs a)
   }
 }
 
+// Compact output: copy slab columns [s0, s0+ls) of the U relaxed rows into the
+// caller's U x wl array.
+__global__ void __launch_bounds__(256) compact_kernel(CompactArgs a) {
+  if (*a.qerr != 0u) return;
+  const uint32_t U = a.counts[0];
+  if ((unsigned long long)U * a.wl > a.rows_cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(a.qerr, 0u, 2u);  // 2 = SVV_ENOMEM
+    return;
+  }
+  const uint32_t lps = __ffs(a.LP) - 1;
+  const unsigned long long n = (unsigned long long)U * a.ls;
+  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t r = (uint32_t)(k / a.ls), i = (uint32_t)(k % a.ls);
+    a.rows_out[(size_t)r * a.wl + a.s0 + i] = a.val[((size_t)r << lps) + i];
+  }
+}
+
+cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s) {
+  compact_kernel<<<1216, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 template <class Op, int P, int K>
 static cudaError_t launch_r(const RelaxArgs& a, LaunchCfg cfg, cudaStream_t s) {

@@ -24,7 +24,8 @@ EXPORTS = ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "sv
            "svv_query_host", "svv_get_bounds", "svv_set_tuning", "svv_get_stats", "svv_device_bytes", "svv_status_str",
            "svv_last_error", "svv_destroy", "svv_solve_snapshot_noalloc",
            "svv_get_round_trace", "svv_query_batch", "svv_serve_start", "svv_submit", "svv_poll",
-           "svv_ticket_info", "svv_release", "svv_serve_stop", "svv_serve_replay", "svv_autotune")
+           "svv_ticket_info", "svv_release", "svv_serve_stop", "svv_serve_replay", "svv_autotune",
+           "svv_query_compact")
 
 
 class SvvError(RuntimeError):
@@ -101,6 +102,8 @@ def lib():
     L.svv_serve_replay.argtypes = [P, u32, ctypes.POINTER(svv_query_spec), P, P, P]
     L.svv_autotune.argtypes = [P, i32, u32, u32, u32, u32, ctypes.POINTER(svv_tune_result)]
     L.svv_autotune.restype = i32
+    L.svv_query_compact.argtypes = [P, i32, u32, u32, u32, P, P, P, u64, ctypes.POINTER(u32), P]
+    L.svv_query_compact.restype = i32
     for f in ("svv_serve_start", "svv_submit", "svv_poll", "svv_ticket_info", "svv_release", "svv_serve_stop",
               "svv_serve_replay"):
         getattr(L, f).restype = i32
@@ -226,6 +229,15 @@ def svv_query_batch(ctx, specs, stream=None):
     if st != 0 and all(x != 0 for x in statuses):
         _check(ctx, st)
     return statuses
+
+
+def svv_query_compact(ctx, qtype: int, source: int, win_begin: int, win_len: int, cap_out, row_out, rows_out,
+                      stream=None) -> int:
+    """Compact result into device tensors; returns U (number of rows)."""
+    u = ctypes.c_uint32()
+    _check(ctx, lib().svv_query_compact(ctx, qtype, source, win_begin, win_len, _ptr(cap_out), _ptr(row_out),
+                                        _ptr(rows_out), rows_out.numel(), ctypes.byref(u), _stream(stream)))
+    return int(u.value)
 
 
 def svv_autotune(ctx, qtype: int, source: int, win_begin: int, win_len: int, reps: int = 3) -> dict:
