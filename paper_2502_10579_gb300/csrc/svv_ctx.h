@@ -116,6 +116,8 @@ struct svv_ctx {
   unsigned long long* trace = nullptr;  // [3][kTraceCap]: intersection, union, relaxation
   bool skip_same = true;                // per-chunk last-relaxed value (procv)
   uint32_t relax_lanes = 32;            // lanes per edge in the relaxation (8, 16, 32)
+  bool pull = true;                     // build the transposed graph at load; pull dense rounds
+  uint32_t pull_pct = 15;               // pull when the frontier holds > pull_pct % of all units
   uint32_t* procv = nullptr;
   uint32_t pcap = 0;
   cudaEvent_t ev[7] = {};

@@ -51,6 +51,17 @@ struct DevGraph {
   const uint64_t* nfmask;   // [NF*W]
   const uint32_t* nfsrc;    // [NF]
   const uint2* nfcw;        // [NF]
+  // Transposed graph for pull rounds (may be absent: irp == nullptr).  Row v
+  // holds v's in-edges (source, weight), those present in all S snapshots
+  // first; the others have W mask words at inmask[(infp[v]+j)*W].  iunits
+  // lists every (vertex, chunk of 2^pull_cs in-edges) once.
+  const uint32_t* irp;      // [V+1]
+  const uint32_t* infp;     // [V+1]
+  const uint2* icw;         // [E]
+  const uint64_t* inmask;   // [NF*W]
+  const unsigned long long* iunits;
+  uint32_t NIU;
+  uint32_t pull_cs;
 };
 
 struct Window {
@@ -84,6 +95,11 @@ struct SolveArgs {
   // again with the same value cannot improve anything).  pcap entries.
   uint32_t* procv;
   uint32_t pcap;
+  // direction switch (needs the transposed graph): a round whose frontier
+  // holds more than pull_units units runs as a pull pass over every vertex's
+  // in-edges; after a pull round that changed more than push_verts vertices the
+  // next round pulls again.  0 disables pulling.
+  uint32_t pull_units, push_verts;
 };
 
 struct QrsArgs {

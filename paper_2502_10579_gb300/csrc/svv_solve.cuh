@@ -102,15 +102,119 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
       break;
     }
     n = min(n, a.qcap);
+    // How this round runs.  After a push round the frontier is a unit queue of
+    // n units; after a pull round it is the n vertices stamped with `it`.  A
+    // large frontier is pulled: every vertex takes the best candidate over
+    // its in-edges (no queue, one atomic per chunk); a small one is pushed.
+    const bool dense = cta_read(&c->aux[3 + cur]) != 0u;
+    const bool can_pull = g.irp != nullptr && a.pull_units != 0u;
+    const bool pull = can_pull && (dense ? (n > a.push_verts) : (n > a.pull_units));
     if (gtid == 0) {
       atomicExch(&c->qn[clr], 0u);
       atomicExch(&c->ticket[clr], 0u);
       atomicExch(&c->aux[clr], 0u);
+      atomicExch(&c->aux[3 + nxt], pull ? 1u : 0u);
+      atomicExch(&c->aux[6 + ((it + 1u) & 1u)], 0u);  // compaction counter of the next round
     }
-    const unsigned long long* qin = (it & 1u) ? a.q1 : a.q0;
+    unsigned long long* qin = (it & 1u) ? a.q1 : a.q0;
     unsigned long long* qout = (it & 1u) ? a.q0 : a.q1;
     unsigned* qn_out = &c->qn[nxt];
     const uint32_t stamp_next = it + 1u;
+
+    if (pull) {
+      // ---- pull round over the transposed graph
+      uint32_t changed = 0;
+      const uint32_t pcs = g.pull_cs;
+      const Batches bp{g.NIU, batch_size(g.NIU, nwarps, 32u), nwarps, gwarp, &c->ticket[cur]};
+      for (uint32_t t0 = bp.first(); t0 < g.NIU; t0 = bp.next(lane)) {
+        const uint32_t ui = t0 + lane;
+        uint32_t v = 0, beg = 0, cnt = 0, fe = 0, nfb = 0;
+        if (lane < bp.tk && ui < g.NIU) {
+          const unsigned long long u = __ldg(g.iunits + ui);
+          v = (uint32_t)u;
+          const uint32_t ch = (uint32_t)(u >> 32);
+          const uint32_t r0 = __ldg(g.irp + v), r1 = __ldg(g.irp + v + 1);
+          const uint32_t nf0 = __ldg(g.infp + v), nf1 = __ldg(g.infp + v + 1);
+          fe = r1 - (nf1 - nf0);
+          nfb = nf0;
+          beg = r0 + (ch << pcs);
+          uint32_t end = min(r1, beg + (1u << pcs));
+          if (PRED == kPredAll && a.skip_nf) end = min(end, fe);
+          cnt = end > beg ? end - beg : 0u;
+        }
+        const uint32_t incl = warp_incl_scan(cnt, lane);
+        const uint32_t total = __shfl_sync(kFullMask, incl, 31);
+        if (lane == 0) relaxed += total;
+        // two 32-edge steps per iteration: both gathers are issued before
+        // either reduction
+        for (uint32_t p0 = 0; p0 < total; p0 += 64u) {
+          int kk[2];
+          uint32_t vk[2], srcv[2], ww[2];
+          bool live[2];
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const uint32_t p = p0 + 32u * j + lane;
+            kk[j] = warp_owner(incl, p < total ? p : total - 1u);
+            const int k = kk[j];
+            const uint32_t ik = __shfl_sync(kFullMask, incl, k);
+            const uint32_t ck = __shfl_sync(kFullMask, cnt, k);
+            const uint32_t bk = __shfl_sync(kFullMask, beg, k);
+            const uint32_t fk = __shfl_sync(kFullMask, fe, k);
+            const uint32_t nk = __shfl_sync(kFullMask, nfb, k);
+            vk[j] = __shfl_sync(kFullMask, v, k);
+            live[j] = false;
+            srcv[j] = 0;
+            ww[j] = 0;
+            if (p < total) {
+              const uint32_t e = bk + (p - (ik - ck));
+              const uint2 ew = __ldg(g.icw + e);
+              bool present = true;
+              if (e >= fk) {
+                const uint64_t* m = g.inmask + (size_t)(nk + (e - fk)) * g.W;
+                if (PRED == kPredAll) present = window_all(m, a.win);
+                else if (PRED == kPredAny) present = window_any(m, a.win);
+                else present = mask_bit(m, a.bit);
+              }
+              live[j] = present;
+              srcv[j] = ew.x;
+              ww[j] = ew.y;
+            }
+          }
+          uint32_t cand[2];
+#pragma unroll
+          for (int j = 0; j < 2; ++j) cand[j] = live[j] ? Op::relax(ld_cg(a.val + srcv[j]), ww[j]) : Op::kIdentity;
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const uint32_t p = p0 + 32u * j + lane;
+            // best candidate per target among the lanes of this step
+            const unsigned grp = __match_any_sync(kFullMask, p < total ? (uint32_t)kk[j] : 64u + lane);
+            const uint32_t best =
+                Op::better(0u, 1u) ? __reduce_min_sync(grp, cand[j]) : __reduce_max_sync(grp, cand[j]);
+            if (p < total && lane == (unsigned)(__ffs(grp) - 1) && Op::better(best, ld_cg(a.val + vk[j]))) {
+              const uint32_t old = Op::atomic(a.val + vk[j], best);
+              if (Op::better(best, old) && atomicExch(a.stamp + vk[j], stamp_next) != stamp_next) ++changed;
+            }
+          }
+        }
+      }
+      const uint32_t wc = __reduce_add_sync(kFullMask, changed);
+      if (lane == 0 && wc) atomicAdd(qn_out, wc);
+      if (!t.sync()) return false;
+      continue;
+    }
+    if (dense) {
+      // ---- the last round pulled: queue the vertices it changed (stamp == it)
+      unsigned* cnt_ctr = &c->aux[6 + (it & 1u)];
+      for (uint32_t v0 = gwarp * 32u; v0 < g.V; v0 += nwarps * 32u) {
+        const uint32_t v = v0 + lane;
+        const bool take = v < g.V && ld_cg(a.stamp + v) == it;
+        const uint32_t deg = take ? (__ldg(g.rp + v + 1) - __ldg(g.rp + v)) : 0u;
+        stage_push_units(take, v, deg, a.cshift, st, qin, cnt_ctr, a.qcap, c, a.qerr, lane);
+      }
+      stage_flush_cta(st, qin, cnt_ctr, a.qcap, c, a.qerr, lane);
+      if (!t.sync()) return false;
+      n = min(cta_read(cnt_ctr), a.qcap);
+    }
     // near-far: relax only units whose value is within delta of the best
     // value queued for this round (that unit itself always qualifies, so every
     // round makes progress); the others are queued again unchanged
