@@ -145,6 +145,7 @@ __device__ __forceinline__ int warp_owner(uint32_t incl, uint32_t p) {
 // ---------------------------------------------------------------------------
 // Edge functions, Table 2.
 struct OpSSSP {  // CASMIN(Val(v), Val(u) + w), saturating
+  static constexpr bool kLevels = false;
   static constexpr uint32_t kIdentity = kInf;
   static constexpr uint32_t kSource = 0;
   __device__ __forceinline__ static uint32_t relax(uint32_t sv, uint32_t w) {
@@ -157,6 +158,7 @@ struct OpSSSP {  // CASMIN(Val(v), Val(u) + w), saturating
 };
 
 struct OpSSWP {  // CASMAX(Val(v), min(Val(u), w))
+  static constexpr bool kLevels = false;
   static constexpr uint32_t kIdentity = 0;
   static constexpr uint32_t kSource = kInf;
   __device__ __forceinline__ static uint32_t relax(uint32_t sv, uint32_t w) { return sv < w ? sv : w; }
@@ -165,6 +167,7 @@ struct OpSSWP {  // CASMAX(Val(v), min(Val(u), w))
 };
 
 struct OpBFS {  // CASMIN(Val(v), Val(u) + 1)
+  static constexpr bool kLevels = true;  // a round from the source sets exactly one level
   static constexpr uint32_t kIdentity = kInf;
   static constexpr uint32_t kSource = 0;
   __device__ __forceinline__ static uint32_t relax(uint32_t sv, uint32_t) { return sv == kInf ? kInf : sv + 1; }
@@ -173,6 +176,7 @@ struct OpBFS {  // CASMIN(Val(v), Val(u) + 1)
 };
 
 struct OpSSNP {  // CASMIN(Val(v), max(Val(u), w))
+  static constexpr bool kLevels = false;
   static constexpr uint32_t kIdentity = kInf;
   static constexpr uint32_t kSource = 0;
   __device__ __forceinline__ static uint32_t relax(uint32_t sv, uint32_t w) {

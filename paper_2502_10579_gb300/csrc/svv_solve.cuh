@@ -125,6 +125,10 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
       // ---- pull round over the transposed graph
       uint32_t changed = 0;
       const uint32_t pcs = g.pull_cs;
+      // BFS from the source: round `it` sets level `it` exactly when it only
+      // takes in-neighbours of level it-1; then every level already set is
+      // final and a visited vertex skips its in-edges (bottom-up BFS)
+      const bool bottom_up = Op::kLevels && a.init == kInitSource;
       const Batches bp{g.NIU, batch_size(g.NIU, nwarps, 32u), nwarps, gwarp, &c->ticket[cur]};
       for (uint32_t t0 = bp.first(); t0 < g.NIU; t0 = bp.next(lane)) {
         const uint32_t ui = t0 + lane;
@@ -141,6 +145,7 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
           uint32_t end = min(r1, beg + (1u << pcs));
           if (PRED == kPredAll && a.skip_nf) end = min(end, fe);
           cnt = end > beg ? end - beg : 0u;
+          if (bottom_up && cnt && ld_cg(a.val + v) != kInf) cnt = 0;
         }
         const uint32_t incl = warp_incl_scan(cnt, lane);
         const uint32_t total = __shfl_sync(kFullMask, incl, 31);
@@ -182,7 +187,13 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
           }
           uint32_t cand[2];
 #pragma unroll
-          for (int j = 0; j < 2; ++j) cand[j] = live[j] ? Op::relax(ld_cg(a.val + srcv[j]), ww[j]) : Op::kIdentity;
+          for (int j = 0; j < 2; ++j) {
+            cand[j] = Op::kIdentity;
+            if (live[j]) {
+              const uint32_t su = ld_cg(a.val + srcv[j]);
+              if (!bottom_up || su < it) cand[j] = Op::relax(su, ww[j]);
+            }
+          }
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
             const uint32_t p = p0 + 32u * j + lane;
