@@ -324,6 +324,7 @@ def run_batch(args, world, rank, local):
     vals = sum(q.win_len * log.V for q in qs)
     value = vals * args.steps * world / (ms / 1e3)
     stats = ctx.stats()
+    one_launch = stats["batch_teams"] > 0
     # the same queries one at a time through svv_query, and a sample of the
     # plain per-snapshot recompute
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -343,16 +344,17 @@ def run_batch(args, world, rank, local):
     plain_value = sum(q.win_len * log.V for q in sample) / (plain_ms / 1e3)
     if rank == 0:
         print(json.dumps({
-            "metric": "snapshot x vertex values/s (batched intersection-union queries, one launch)",
+            "metric": "snapshot x vertex values/s (batched intersection-union queries, svv_query_batch)",
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
-            "config": {"workload": desc, "queries": nq, "output_bytes": int(vals * 4), "teams": stats["batch_teams"],
-                       "team_blocks": stats["batch_team_blocks"],
+            "config": {"workload": desc, "queries": nq, "output_bytes": int(vals * 4),
+                       "mode": "one launch" if one_launch else "in order",
+                       "teams": stats["batch_teams"], "team_blocks": stats["batch_team_blocks"],
                        "tuning": dict(kv.split("=", 1) for kv in args.tune)},
             "one_at_a_time": {"value": vals / (seq_ms / 1e3), "unit": UNIT, "ms": seq_ms},
             "plain_sample": {"value": plain_value, "unit": UNIT, "queries": len(sample), "ms": plain_ms},
-            "clocks": clocks, "gpu_launches": args.steps}), flush=True)
+            "clocks": clocks, "gpu_launches": args.steps * (1 if one_launch else 5 * nq)}), flush=True)
     ctx.close()
     return 0
 
@@ -413,8 +415,10 @@ def run_rmat24(args, world, rank, local):
 def run_serve(args, world, rank, local):
     """Poisson request streams at 100, 1,000 and 10,000 requests/s (type
     uniform, source uniform, L uniform in [8, 100] at a uniform offset) served
-    by the live batch kernel with arena admission; the plain per-snapshot
-    recompute served FIFO on the first requests of the 100/s stream."""
+    with arena admission -- by the live batch kernel below 2M vertices, in
+    order (each request as svv_query's kernels) from 2M; the plain
+    per-snapshot recompute served FIFO on the first requests of the 100/s
+    stream."""
     import torch
 
     import __graft_entry__
@@ -431,6 +435,8 @@ def run_serve(args, world, rank, local):
     ctx = _setup_ctx(svv, log, dev, args)
     arena = (64 << 30) if args.workload == "serve22" else (2 << 30)
     svv.svv_serve_start(ctx.h, max_window=min(100, log.S), capacity=1 << 16, arena_bytes=arena)
+    bm = int(dict(kv.split("=", 1) for kv in args.tune).get("batch_mode", 0))
+    mode = "in order" if bm == 2 or (bm == 0 and log.V >= (2 << 20)) else "live kernel"
     dur = args.serve_seconds
     warm = 1.0
     results = {}
@@ -473,7 +479,8 @@ def run_serve(args, world, rank, local):
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": desc + f"; Poisson 100/1,000/10,000 req/s, each stream min({dur:g} s, 2,500 requests), "
                                    "first 10% excluded",
-                       "arena_bytes": arena, "admission": "output arena (svv_submit refuses when full)"},
+                       "arena_bytes": arena, "admission": "output arena (svv_submit refuses when full)",
+                       "mode": mode},
             "serve": results, "plain_fifo": plain}), flush=True)
     ctx.close()
     return 0

@@ -134,19 +134,23 @@ svv_status svv_load(svv_ctx *ctx, uint32_t V, uint64_t E, uint32_t S, const uint
 svv_status svv_query(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
                      uint32_t win_len, uint32_t *out, void *cuda_stream);
 
-/* Many queries in ONE persistent launch (the instances may mix types, sources
- * and window lengths).  The cooperative grid is split into teams of CTAs;
- * each team takes instances from a device work queue and runs the whole
- * intersection-union pipeline of svv_query for each, with its own scratch, so
- * instances overlap on the GPU.  Each spec is checked as in svv_query; an
- * invalid spec gets SVV_EINVAL and is skipped.  Every valid spec's `out` is
- * written as svv_query would write it, and its status is set (SVV_OK, or
- * SVV_ETIMEOUT for an instance that hit a bounded wait or was not reached
- * because its team stopped).  The call returns after the stream reaches the
- * end of the batch, with SVV_OK if every spec succeeded, else the first
- * failing status.  The number of teams ("batch_teams" tuning key, default 8)
- * is reduced when their scratch would exceed the HBM budget; SVV_ENOMEM if not
- * even one team fits. */
+/* Many queries in one call (the instances may mix types, sources and window
+ * lengths).  On graphs below 2M vertices the batch runs as ONE persistent
+ * launch: the cooperative grid is split into teams of CTAs; each team takes
+ * instances from a device work queue and runs the whole intersection-union
+ * pipeline of svv_query for each, with its own scratch, so instances overlap
+ * on the GPU.  From 2M vertices, where one query's rounds already fill the
+ * GPU, the instances run in order with svv_query's per-phase kernels, each
+ * instance's status kept on the device and read back once at the end
+ * ("batch_mode" tuning key: 0 = by graph size, 1 = one launch, 2 = in order).
+ * Each spec is checked as in svv_query; an invalid spec gets SVV_EINVAL and
+ * is skipped.  Every valid spec's `out` is written as svv_query would write
+ * it, and its status is set (SVV_OK, or SVV_ETIMEOUT for an instance that hit
+ * a bounded wait or was not reached because its team stopped).  The call
+ * returns after the stream reaches the end of the batch, with SVV_OK if every
+ * spec succeeded, else the first failing status.  In one-launch mode the
+ * number of teams ("batch_teams" tuning key) is reduced when their scratch
+ * would exceed the HBM budget; SVV_ENOMEM if not even one team fits. */
 svv_status svv_query_batch(svv_ctx *ctx, uint32_t n, svv_query_spec *specs, void *cuda_stream);
 
 /* ---- Serving: requests that arrive while others run -------------------------
@@ -159,9 +163,20 @@ svv_status svv_query_batch(svv_ctx *ctx, uint32_t n, svv_query_spec *specs, void
  * leaves); a request that does not fit is refused with SVV_EBUSY until earlier
  * results are released -- that is the admission control.  The kernel leaves
  * after an idle period and is relaunched by the next svv_submit or svv_poll.
+ * That is the mode below 2M vertices.  From 2M vertices ("batch_mode" as set
+ * when the server starts: 0 = by graph size, 1 = live kernel, 2 = in order),
+ * where one request already fills the GPU, svv_submit queues the request's
+ * svv_query kernels on the library stream behind the earlier ones, framed by
+ * two one-thread marker launches that write its times, status and completion
+ * flag to the same mapped memory; requests then run one after another, each
+ * on the whole GPU.  In that mode the server shares svv_query's scratch:
+ * svv_query, svv_query_compact, svv_query_plain, svv_query_batch and
+ * svv_get_bounds on another stream are ordered after the requests submitted
+ * before them (stream waits, no host wait), and later requests after them.
  * max_window bounds win_len; capacity is the number of requests that may be
- * submitted and not yet released.  SVV_ENOMEM if the team scratch or the
- * arena does not fit the budget. */
+ * submitted and not yet released.  SVV_ENOMEM if the team scratch (or, in
+ * order, the query scratch for max_window) or the arena does not fit the
+ * budget. */
 svv_status svv_serve_start(svv_ctx *ctx, uint32_t max_window, uint32_t capacity,
                            uint64_t arena_bytes);
 
@@ -178,7 +193,7 @@ svv_status svv_submit(svv_ctx *ctx, const svv_query_spec *spec, uint64_t *ticket
 svv_status svv_poll(svv_ctx *ctx, uint64_t ticket, int wait, svv_status *result);
 
 /* The device buffer holding a request's output (its own or the arena's) and
- * the device times (ns, %globaltimer) at which a team started and finished it.
+ * the device times (ns, %globaltimer) at which it started and finished.
  * Valid until svv_release. */
 svv_status svv_ticket_info(svv_ctx *ctx, uint64_t ticket, uint32_t **out,
                            uint64_t *device_start_ns, uint64_t *device_end_ns);
@@ -195,7 +210,8 @@ svv_status svv_release(svv_ctx *ctx, uint64_t ticket);
 svv_status svv_serve_replay(svv_ctx *ctx, uint32_t n, const svv_query_spec *specs,
                             const double *arrival_s, double *latency_ms, double *done_s);
 
-/* Stop the server (pending requests are abandoned) and free its memory. */
+/* Stop the server and free its memory (live mode abandons pending requests;
+ * in order, the call waits for the queued ones). */
 svv_status svv_serve_stop(svv_ctx *ctx);
 
 /* svv_query without the dense output (the paper keeps one result array per
@@ -302,7 +318,8 @@ svv_status svv_autotune(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t w
  * replays it; falls back to direct launches where capture is refused; phase
  * timing is not recorded in this mode),
  * "batch_teams" (teams of svv_query_batch and the server, 1..64; 0 = by graph
- * size: 8 up to 1M vertices, fewer above, 1 from 8M), "relax_lanes" (8, 16, 32:
+ * size: 8 up to 1M vertices, fewer above, 1 from 8M), "batch_mode" (0 = by
+ * graph size, 1 = one launch, 2 = in order; see svv_query_batch), "relax_lanes" (8, 16, 32:
  * lanes per edge in the relaxation), "skip_same" (1 = skip work chunks already
  * relaxed with their vertex's current value), "round_trace" (1 = record, per frontier round of the intersection solve,
  * the union solve and the relaxation, the frontier size and a device

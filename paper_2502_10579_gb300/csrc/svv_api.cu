@@ -49,6 +49,9 @@ svv_status ensure_window(svv_ctx* c, uint32_t L) {
   uint32_t P, K;
   slab_shape(std::min(L, c->slab_max), P, K);
   const uint64_t need_v = (uint64_t)std::max<uint32_t>(c->g.V, 1) * P * K;
+  // an in-order server's queued requests still read the old buffers
+  if ((need_m > c->mcap || need_v > c->valcap) && c->serve.active && c->serve.stream)
+    cudaStreamSynchronize(c->serve.stream);
   if (need_m > c->mcap) {
     if (c->qmask) {
       auto it = std::find(c->scratch_bufs.begin(), c->scratch_bufs.end(), (void*)c->qmask);
@@ -204,6 +207,8 @@ void svv_destroy(svv_ctx* c) {
     if (c->hqerr) cudaFreeHost(c->hqerr);
     for (auto& e : c->ev)
       if (e) cudaEventDestroy(e);
+    for (auto& e : c->bev)
+      if (e) cudaEventDestroy(e);
     if (c->trace) cudaFree(c->trace);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -263,6 +268,9 @@ svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
   } else if (k == "skip_same") {
     if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "skip_same is 0 or 1");
     c->skip_same = v != 0;
+  } else if (k == "batch_mode") {
+    if (v < 0 || v > 2) return fail(c, SVV_EINVAL, "batch_mode is 0 (by graph size), 1 (one launch) or 2 (in order)");
+    c->batch_mode = (int)v;
   } else if (k == "batch_teams") {
     if (v < 0 || v > 64) return fail(c, SVV_EINVAL, "batch_teams in [0, 64]");
     c->batch_teams = (int)v;
@@ -761,6 +769,48 @@ svv_status graph_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32_t
 
 }  // namespace
 
+namespace svv {
+
+// In-order batch: the instances run one after another with the per-phase
+// kernels on one stream.  Each instance's error word is copied to its own
+// device slot, and all are read back once at the end, so nothing waits on the
+// host between instances.
+svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, uint32_t* qerr_dev, uint32_t* qerr_host,
+                          cudaStream_t s, float* ms) {
+  uint32_t Lmax = 1;
+  for (uint32_t k = 0; k < m; ++k) Lmax = std::max(Lmax, inst[k].wl);
+  svv_status st = ensure_window(c, Lmax);
+  if (st) return st;
+  cudaError_t e = cudaSuccess;
+  for (auto& ev : c->bev)
+    if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+  cudaEventRecord(c->bev[0], s);
+  for (uint32_t k = 0; k < m; ++k) {
+    float a = 0.f, b = 0.f;
+    if ((st = enqueue_query(c, inst[k].type, inst[k].source, inst[k].wb, inst[k].wl, inst[k].out, s, false, &a, &b)))
+      return st;
+    if ((e = cudaMemcpyAsync(qerr_dev + k, c->qerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return cuda_fail(c, e, "batch status copy");
+  }
+  cudaEventRecord(c->bev[1], s);
+  e = cudaMemcpyAsync(qerr_host, qerr_dev, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch");
+  *ms = 0.f;
+  cudaEventElapsedTime(ms, c->bev[0], c->bev[1]);
+  return SVV_OK;
+}
+
+svv_status reserve_window(svv_ctx* c, uint32_t L) { return ensure_window(c, L); }
+
+// One request of an in-order server: svv_query's kernels, no host wait.
+svv_status enqueue_instance(svv_ctx* c, const BatchInstance& q, cudaStream_t s) {
+  float a = 0.f, b = 0.f;
+  return enqueue_query(c, q.type, q.source, q.wb, q.wl, q.out, s, false, &a, &b);
+}
+
+}  // namespace svv
+
 extern "C" {
 
 svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, uint32_t wl, uint32_t* out,
@@ -770,6 +820,7 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
   DeviceGuard dg(c->device);
   if ((st = ensure_window(c, wl))) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  ServeFence fence(c, s);
   const int t = (int)type;
   bool timing = c->phase_timing;
   float ms_relax = 0.f, ms_scatter = 0.f;
@@ -819,6 +870,7 @@ svv_status svv_query_compact(svv_ctx* c, svv_type type, uint32_t source, uint32_
   DeviceGuard dg(c->device);
   if ((st = ensure_window(c, wl))) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  ServeFence fence(c, s);
   const CompactOut co{cap_out, row_out, rows_out, rows_cap};
   float a = 0.f, b = 0.f;
   if ((st = enqueue_query(c, (int)type, source, wb, wl, nullptr, s, false, &a, &b, &co))) return st;
@@ -837,6 +889,7 @@ svv_status svv_query_plain(svv_ctx* c, svv_type type, uint32_t source, uint32_t 
   if (st) return st;
   DeviceGuard dg(c->device);
   cudaStream_t s = (cudaStream_t)stream;
+  ServeFence fence(c, s);
   const uint32_t nslot = std::min<uint32_t>(wl, kNumCtl - 8);
   cudaError_t e = cudaMemsetAsync(c->ctl + 8, 0, sizeof(TeamCtl) * nslot, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->qerr, 0, sizeof(uint32_t), s);
@@ -877,6 +930,7 @@ svv_status svv_get_bounds(svv_ctx* c, uint32_t* cap, uint32_t* cup, uint32_t* ro
   if (!c->loaded) return fail(c, SVV_ENOTLOADED, "no graph loaded");
   DeviceGuard dg(c->device);
   cudaStream_t s = (cudaStream_t)stream;
+  ServeFence fence(c, s);
   const size_t n = (size_t)c->g.V * sizeof(uint32_t);
   cudaError_t e = cudaSuccess;
   if (cap) e = cudaMemcpyAsync(cap, c->rI, n, cudaMemcpyDeviceToDevice, s);

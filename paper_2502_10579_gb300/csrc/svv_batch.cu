@@ -87,6 +87,12 @@ __device__ bool run_instance(const BatchArgs& b, const BatchInstance& q, uint32_
   const unsigned long long cap = a.delta ? 16ull * b.g.V + 64 : (unsigned long long)b.g.V + 2;
   a.maxit = b.maxit ? b.maxit : (uint32_t)min(cap, 0xFFFFFFF0ull);
   a.spin_ns = b.spin_ns;
+  a.pull_units = b.pull_units;
+  a.push_verts = b.push_verts;
+  if (b.skip_same && sc.procv) {
+    a.procv = sc.procv;
+    a.pcap = b.g.V + (b.g.E >> b.solve_cs) + 2u;
+  }
 
   // intersection graph
   a.init = kInitSource;

@@ -14,9 +14,6 @@ void free_batch(svv_ctx* c) {
   p = BatchPool{};
 }
 
-namespace {
-}  // namespace
-
 // bytes one team needs for windows up to L (its share of query scratch)
 static uint64_t team_bytes(const svv_ctx* c, uint32_t LP, uint32_t QW, uint32_t team_blocks) {
   const uint64_t V = c->g.V, E = std::max<uint32_t>(c->g.E, 1), NF = std::max<uint32_t>(c->g.NF, 1);
@@ -31,6 +28,7 @@ static uint64_t team_bytes(const svv_ctx* c, uint32_t LP, uint32_t QW, uint32_t 
   b += round256(NF * QW * 8);                // qmask
   b += round256(V * LP * 4);                 // val
   b += 2 * round256(qcap * 8) + round256(ucap * 8);
+  b += round256((V + (E >> 4) + 64) * 4);  // procv
   return b;
 }
 
@@ -47,8 +45,9 @@ static svv_status alloc_team(svv_ctx* c, std::vector<void*>& owner, uint32_t LP,
       (st = alloc_n(c, owner, V, &t.qrow)) || (st = alloc_n(c, owner, E, &t.qcw)) ||
       (st = alloc_n(c, owner, NF * QW, &t.qmask)) || (st = alloc_n(c, owner, V * LP, &t.val)) ||
       (st = alloc_n(c, owner, qcap, &t.q0)) || (st = alloc_n(c, owner, qcap, &t.q1)) ||
-      (st = alloc_n(c, owner, ucap, &t.units)))
+      (st = alloc_n(c, owner, ucap, &t.units)) || (st = alloc_n(c, owner, V + (E >> 4) + 64, &t.procv)))
     return st;
+  t.pcap = (uint32_t)(V + (E >> 4) + 64);
   t.qcap = (uint32_t)qcap;
   t.ucap = (uint32_t)ucap;
   t.ecap = (uint32_t)E;
@@ -65,7 +64,8 @@ svv_status ensure_pool(svv_ctx* c, int want_teams, uint32_t L) {
   const int per_sm = std::max(1, std::min(c->occ_batch, 2));
   const int total_blocks = c->num_sms * per_sm;
   want_teams = std::max(1, std::min(want_teams, total_blocks));
-  if (p.teams >= want_teams && p.LP >= LP && p.QW >= QW) return SVV_OK;
+  // the grid is split evenly, so a different team count needs a new pool
+  if (p.teams && p.want == want_teams && p.LP >= LP && p.QW >= QW) return SVV_OK;
   // (re)build
   for (void* b : p.bufs) cudaFree(b);
   c->allocated -= std::min<uint64_t>(c->allocated, p.bytes);
@@ -84,12 +84,13 @@ svv_status ensure_pool(svv_ctx* c, int want_teams, uint32_t L) {
   std::vector<TeamScratch> host(teams);
   svv_status st;
   for (int i = 0; i < teams; ++i)
-    if ((st = alloc_team(c, p.bufs, LP, QW, team_blocks, host[i]))) return st;
+    if ((st = alloc_team(c, p.bufs, LP, QW, (uint32_t)total_blocks, host[i]))) return st;  // any team size
   if ((st = alloc_n(c, p.bufs, (uint64_t)teams, &p.d_sc)) ||
       (st = alloc_n(c, p.bufs, (uint64_t)teams * kBatchCtl, &p.d_ctl)))
     return st;
   cudaError_t e = cudaMemcpy(p.d_sc, host.data(), sizeof(TeamScratch) * teams, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(c, e, "uploading team scratch");
+  p.want = want_teams;
   p.teams = teams;
   p.team_blocks = team_blocks;
   p.LP = LP;
@@ -132,6 +133,15 @@ int default_teams(const svv_ctx* c) {
   return (int)std::max<uint64_t>(1, std::min<uint64_t>(8, t));
 }
 
+// One launch for the batch, or the instances in order (svv_query's kernels).
+// From 2M vertices a query's big rounds already fill the GPU and the
+// per-phase kernels run at higher occupancy than the all-phase batch kernel,
+// so teams sharing the grid lose to queries in order.
+bool batch_one_launch(const svv_ctx* c) {
+  if (c->batch_mode) return c->batch_mode == 1;
+  return c->g.V < (2u << 20);
+}
+
 BatchArgs batch_args(svv_ctx* c) {
   BatchPool& p = c->batch;
   BatchArgs b{};
@@ -152,6 +162,12 @@ BatchArgs batch_args(svv_ctx* c) {
   b.delta[1] = c->delta[1];
   b.maxit = c->maxit;
   b.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
+  b.skip_same = c->skip_same ? 1u : 0u;
+  if (c->g.irp && c->pull_pct) {
+    const uint64_t all_units = (uint64_t)c->g.V + (c->g.E >> c->solve_cs);
+    b.pull_units = (uint32_t)std::max<uint64_t>(1, all_units * c->pull_pct / 100);
+    b.push_verts = (uint32_t)std::max<uint64_t>(1, (uint64_t)c->g.V * c->pull_pct / 100);
+  }
   return b;
 }
 
@@ -196,11 +212,32 @@ extern "C" svv_status svv_query_batch(svv_ctx* c, uint32_t n, svv_query_spec* sp
   }
   if (inst.empty()) return fail(c, first_bad, "no valid query in the batch");
   const uint32_t m = (uint32_t)inst.size();
-  svv_status st = ensure_pool(c, std::min<int>(default_teams(c), (int)m), Lmax);
-  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  svv_status st;
+  if (!batch_one_launch(c)) {
+    if ((st = ensure_instances(c, m))) return st;
+    std::vector<uint32_t> qerr(m);
+    float ms = 0.f;
+    {
+      ServeFence fence(c, s);
+      if ((st = batch_in_order(c, inst.data(), m, c->batch.d_qerr, qerr.data(), s, &ms))) return st;
+    }
+    svv_status overall = first_bad;
+    for (uint32_t k = 0; k < m; ++k) {
+      const svv_status si = status_of(qerr[k], 1u);
+      specs[idx[k]].status = si;
+      if (si && !overall) overall = si;
+    }
+    c->stats = svv_stats{};
+    c->stats.ms_batch = ms;
+    c->stats.batch_teams = 0;
+    if (overall) return fail(c, overall, "some batched queries failed");
+    c->err.clear();
+    return SVV_OK;
+  }
+  if ((st = ensure_pool(c, default_teams(c), Lmax))) return st;
   if ((st = ensure_instances(c, m))) return st;
   BatchPool& p = c->batch;
-  cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(p.d_inst, inst.data(), sizeof(BatchInstance) * m, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.d_ctl, 0, sizeof(TeamCtl) * kBatchCtl * p.teams, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.d_next, 0, sizeof(unsigned), s);
@@ -209,8 +246,10 @@ extern "C" svv_status svv_query_batch(svv_ctx* c, uint32_t n, svv_query_spec* sp
   if (e != cudaSuccess) return cuda_fail(c, e, "batch setup");
   BatchArgs b = batch_args(c);
   b.n_inst = m;
+  // fewer instances than teams: fewer, larger teams over the same grid
   const int teams = std::min<int>(p.teams, (int)m);
-  if ((e = launch_batch(b, LaunchCfg{teams * (int)p.team_blocks, 512}, s)) != cudaSuccess)
+  b.team_blocks = (uint32_t)(p.teams * (int)p.team_blocks / teams);
+  if ((e = launch_batch(b, LaunchCfg{teams * (int)b.team_blocks, 512}, s)) != cudaSuccess)
     return cuda_fail(c, e, "launch batch");
   std::vector<uint32_t> qerr(m), done(m);
   std::vector<unsigned long long> t0(m), t1(m);
@@ -234,7 +273,7 @@ extern "C" svv_status svv_query_batch(svv_ctx* c, uint32_t n, svv_query_spec* sp
   c->stats = svv_stats{};
   c->stats.ms_batch = hi > lo ? (float)((hi - lo) / 1e6) : 0.f;
   c->stats.batch_teams = (uint32_t)teams;
-  c->stats.batch_team_blocks = p.team_blocks;
+  c->stats.batch_team_blocks = b.team_blocks;
   if (overall) return fail(c, overall, "some batched queries failed");
   c->err.clear();
   return SVV_OK;

@@ -30,7 +30,8 @@ struct DeviceGuard {
 
 // scratch of the batch kernel's teams, sized for a window length
 struct BatchPool {
-  int teams = 0;
+  int want = 0;   // teams asked for when the pool was built
+  int teams = 0;  // teams built (fewer when the budget is short)
   uint32_t team_blocks = 0;
   uint32_t LP = 0, QW = 0;
   TeamScratch* d_sc = nullptr;
@@ -91,6 +92,9 @@ struct ServeState {
   std::vector<void*> bufs;
   uint64_t bytes = 0;
   unsigned long long idle_ns = 200000000ull;
+  // in-order mode: each request runs svv_query's kernels on `stream`
+  bool in_order = false;
+  cudaEvent_t ord = nullptr;  // orders other streams' use of the query scratch
 };
 
 }  // namespace svv
@@ -166,7 +170,9 @@ struct svv_ctx {
   svv::BatchPool batch;
   svv::ServeState serve;
   int batch_teams = 0;  // 0: from the graph size
+  int batch_mode = 0;   // 0: by graph size, 1: one launch, 2: in order
   int occ_batch = 0;
+  cudaEvent_t bev[2] = {};  // span of an in-order batch
 
   svv_stats stats{};
 };
@@ -248,5 +254,21 @@ int default_teams(const svv_ctx* c);
 svv_status ensure_pool(svv_ctx* c, int want_teams, uint32_t L);
 svv_status status_of(uint32_t qerr, uint32_t done);
 svv_status check_spec(const svv_ctx* c, const svv_query_spec& q);
+bool batch_one_launch(const svv_ctx* c);
+svv_status reserve_window(svv_ctx* c, uint32_t L);
+svv_status enqueue_instance(svv_ctx* c, const BatchInstance& q, cudaStream_t s);
+
+// While an in-order server is active it shares the single-query scratch: a
+// call that uses that scratch on another stream is ordered after the requests
+// already submitted, and the requests submitted later after the call.
+struct ServeFence {
+  svv_ctx* c;
+  cudaStream_t s;
+  bool on;
+  ServeFence(svv_ctx* c, cudaStream_t s);
+  ~ServeFence();
+};
+svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, uint32_t* qerr_dev, uint32_t* qerr_host,
+                          cudaStream_t s, float* ms);
 
 }  // namespace svv

@@ -199,6 +199,8 @@ struct TeamScratch {
   unsigned long long *q0, *q1, *units;
   uint32_t qcap, ucap, ecap;
   unsigned long long mcap;
+  uint32_t* procv;  // per-chunk last-relaxed values (pcap entries)
+  uint32_t pcap;
 };
 
 constexpr int kBatchCtl = 5;  // per team: barrier, intersection, union, extraction, relaxation
@@ -226,6 +228,8 @@ struct BatchArgs {
   uint32_t delta[2];
   uint32_t maxit;                   // 0 = per-instance default
   unsigned long long spin_ns;
+  uint32_t pull_units, push_verts;  // direction switch of the solves (0 = push only)
+  uint32_t skip_same;               // per-chunk last-relaxed value skip in the solves
 };
 
 // launch helpers (defined in the .cu files)

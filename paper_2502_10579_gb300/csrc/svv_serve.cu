@@ -1,6 +1,13 @@
 // svv_serve.cu -- the serving loop: requests arrive while others run.
 //
-// The batch kernel runs in live mode on a library stream.  svv_submit writes
+// Two modes, chosen like svv_query_batch's: below 2M vertices the batch
+// kernel runs in live mode (below); from 2M vertices, where one request's
+// rounds fill the GPU, each request is queued on the library stream as
+// svv_query's kernels between two one-thread marker launches that write its
+// start time, and its status, end time and completion flag, into the same
+// mapped memory the live kernel uses -- so svv_poll and admission are shared.
+//
+// Live mode: the batch kernel runs on a library stream.  svv_submit writes
 // the request into a ring of instances in host-mapped pinned memory and raises
 // the tail; an idle team picks it up within microseconds, so requests that
 // arrive while others are on the GPU start as soon as a team is free (teams
@@ -16,8 +23,36 @@
 #include <thread>
 
 #include "svv_ctx.h"
+#include "svv_device.cuh"
 
 namespace svv {
+
+// In-order request marker: the start time, or (done != nullptr) the request's
+// error word, end time and completion flag.  The flag is written last, after a
+// system-scope fence, so a host that sees it sees the rest.
+__global__ void serve_mark_kernel(const uint32_t* qerr, uint32_t* qerr_out, uint32_t* done,
+                                  unsigned long long* t) {
+  if (done) *qerr_out = *reinterpret_cast<const volatile uint32_t*>(qerr);
+  *t = global_ns();
+  if (done) {
+    __threadfence_system();
+    *reinterpret_cast<volatile uint32_t*>(done) = 1u;
+  }
+}
+
+ServeFence::ServeFence(svv_ctx* c_, cudaStream_t s_) : c(c_), s(s_), on(false) {
+  ServeState& v = c->serve;
+  if (!v.active || !v.in_order || s == v.stream) return;
+  if (cudaEventRecord(v.ord, v.stream) == cudaSuccess && cudaStreamWaitEvent(s, v.ord, 0) == cudaSuccess) on = true;
+  else cudaStreamSynchronize(v.stream);
+}
+
+ServeFence::~ServeFence() {
+  if (!on) return;
+  ServeState& v = c->serve;
+  if (cudaEventRecord(v.ord, s) != cudaSuccess || cudaStreamWaitEvent(v.stream, v.ord, 0) != cudaSuccess)
+    cudaStreamSynchronize(s);
+}
 
 void free_serve(svv_ctx* c) {
   ServeState& v = c->serve;
@@ -37,6 +72,7 @@ void free_serve(svv_ctx* c) {
   for (void* b : v.bufs) cudaFree(b);
   c->allocated -= std::min<uint64_t>(c->allocated, v.bytes);
   if (v.ev) cudaEventDestroy(v.ev);
+  if (v.ord) cudaEventDestroy(v.ord);
   if (v.stream) cudaStreamDestroy(v.stream);
   v = ServeState{};
 }
@@ -84,6 +120,7 @@ svv_status launch_live(svv_ctx* c) {
 // relaunch the live kernel if it has left while requests are waiting
 svv_status ensure_running(svv_ctx* c) {
   ServeState& v = c->serve;
+  if (v.in_order) return SVV_OK;  // every request was queued when submitted
   if (!v.launched) return launch_live(c);
   const cudaError_t q = cudaEventQuery(v.ev);
   if (q == cudaErrorNotReady) return SVV_OK;
@@ -158,9 +195,10 @@ svv_status svv_serve_start(svv_ctx* c, uint32_t max_window, uint32_t capacity, u
   if (max_window == 0 || max_window > c->g.S) return fail(c, SVV_EINVAL, "max_window must be in [1, S]");
   if (capacity == 0 || capacity > (1u << 24)) return fail(c, SVV_EINVAL, "capacity must be in [1, 2^24]");
   DeviceGuard dg(c->device);
-  svv_status st = ensure_pool(c, default_teams(c), max_window);
-  if (st) return st;
   ServeState& v = c->serve;
+  v.in_order = !batch_one_launch(c);
+  svv_status st = v.in_order ? reserve_window(c, max_window) : ensure_pool(c, default_teams(c), max_window);
+  if (st) return st;
   v.cap = capacity;
   v.maxL = max_window;
   if ((st = host_mapped(c, capacity, &v.h_inst, &v.d_inst)) || (st = host_mapped(c, 2, &v.h_ctrl, &v.d_ctrl)) ||
@@ -187,6 +225,7 @@ svv_status svv_serve_start(svv_ctx* c, uint32_t max_window, uint32_t capacity, u
   cudaError_t e = cudaMemset(v.d_next, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v.stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v.ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v.ord, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     free_serve(c);
     return cuda_fail(c, e, "serve start");
@@ -222,6 +261,22 @@ svv_status svv_submit(svv_ctx* c, const svv_query_spec* spec, uint64_t* ticket) 
   reinterpret_cast<volatile uint32_t*>(v.h_qerr)[slot] = 0u;
   reinterpret_cast<volatile uint32_t*>(v.h_done)[slot] = 0u;
   std::atomic_thread_fence(std::memory_order_seq_cst);
+  if (v.in_order) {
+    serve_mark_kernel<<<1, 1, 0, v.stream>>>(nullptr, nullptr, nullptr, v.d_t0 + slot);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && (st = enqueue_instance(c, v.h_inst[slot], v.stream)) == SVV_OK) {
+      serve_mark_kernel<<<1, 1, 0, v.stream>>>(c->qerr, v.d_qerr + slot, v.d_done + slot, v.d_t1 + slot);
+      e = cudaGetLastError();
+    }
+    if (st || e != cudaSuccess) {
+      if (use_arena) arena_free(v, off);
+      s = ServeSlot{};
+      return st ? st : cuda_fail(c, e, "queueing a request");
+    }
+    *ticket = v.tail++;
+    c->err.clear();
+    return SVV_OK;
+  }
   *ticket = v.tail;
   v.tail++;
   reinterpret_cast<volatile uint32_t*>(v.h_ctrl)[0] = (uint32_t)v.tail;

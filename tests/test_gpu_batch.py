@@ -59,6 +59,25 @@ def test_batch_teams_and_two_words(svv, teams):
             np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L))
 
 
+def test_batch_in_order_mode(svv):
+    """batch_mode 2 runs the instances one after another with svv_query's
+    kernels; results and per-spec statuses are the same as in one launch."""
+    log = W.scaled_rmat(scale=12, edge_factor=8, n_snapshots=100, rate=0.003, seed=17, add_mode="skewed")
+    specs = _mixed(log, 12, 21) + [(3, 1, 0, 100)]
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        ctx.set_tuning("batch_mode", 2)
+        outs, st = ctx.query_batch(specs)
+        assert st == [0] * len(specs)
+        assert ctx.stats()["batch_teams"] == 0
+        for (t, s, b, L), o in zip(specs, outs):
+            np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L))
+        good = ctx.empty_out(4)
+        st = svv.svv_query_batch(ctx.h, [(0, log.V, 0, 4, good), (1, 0, 0, 4, good)])
+        assert st == [1, 0]
+        np.testing.assert_array_equal(svv.to_u32(good), oracle.query(log, 1, 0, 0, 4))
+
+
 def test_batch_invalid_spec_is_skipped(svv):
     log = W.small_rmat()
     with svv.Context(0) as ctx:

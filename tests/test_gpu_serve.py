@@ -89,3 +89,48 @@ def test_serve_admission_and_relaunch(svv):
         with pytest.raises(svv.SvvError):
             svv.svv_submit(ctx.h, 0, 0, 0, 9)  # longer than max_window
         svv.svv_serve_stop(ctx.h)
+
+
+def test_serve_in_order(svv):
+    """batch_mode 2: each request is queued as svv_query's kernels on the
+    server's stream; requests run one after another, a query on another stream
+    in between is ordered with them, and admission still refuses a full arena."""
+    log = W.scaled_rmat(scale=13, edge_factor=8, n_snapshots=100, rate=0.003, seed=56, add_mode="skewed")
+    reqs = _requests(log, 16, 11, 100)
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        alone = [svv.to_u32(ctx.query(t, s, b, L)) for t, s, b, L in reqs]
+        ctx.set_tuning("batch_mode", 2)
+        svv.svv_serve_start(ctx.h, max_window=100, capacity=32, arena_bytes=300 * log.V * 4)
+        side = torch.cuda.Stream()
+        pending, spans, refused = [], [], 0
+
+        def finish_oldest():
+            tk, want = pending.pop(0)
+            assert svv.svv_poll(ctx.h, tk, wait=True) == 0
+            addr, t0, t1 = svv.svv_ticket_info(ctx.h, tk)
+            L = want.shape[0]
+            np.testing.assert_array_equal(svv.device_u32(addr, L * log.V).reshape(L, log.V), want)
+            spans.append((t0, t1))
+            svv.svv_release(ctx.h, tk)
+
+        for k, (r, want) in enumerate(zip(reqs, alone)):
+            tk = svv.svv_submit(ctx.h, *r)
+            while tk is None:  # arena full: finish the oldest, then retry
+                refused += 1
+                finish_oldest()
+                tk = svv.svv_submit(ctx.h, *r)
+            pending.append((tk, want))
+            if k == 4:  # a query on another stream while requests are queued
+                t, s, b, L = reqs[0]
+                mid = ctx.query(t, s, b, L, stream=side)
+        side.synchronize()
+        np.testing.assert_array_equal(svv.to_u32(mid), alone[0])
+        while pending:
+            finish_oldest()
+        assert refused > 0
+        assert all(t0 < t1 for t0, t1 in spans)
+        assert all(spans[i + 1][0] >= spans[i][1] for i in range(len(spans) - 1))  # one after another
+        svv.svv_serve_stop(ctx.h)
+        t, s, b, L = reqs[1]
+        np.testing.assert_array_equal(alone[1], oracle.query(log, t, s, b, L))
