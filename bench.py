@@ -168,7 +168,8 @@ def algo_bytes(phase, gc, st, L):
     return 0
 
 
-KERNEL_SOURCES = {"cap": ["svv_solve.cu", "svv_device.cuh", "svv_push.cuh", "svv_internal.h"]}
+KERNEL_SOURCES = {"cap": ["svv_solve.cu", "svv_solve.cuh", "svv_team.cuh", "svv_device.cuh", "svv_push.cuh",
+                          "svv_internal.h"]}
 
 
 def recorded_traffic(kernel, workload):
