@@ -107,7 +107,7 @@ SolveArgs solve_base(svv_ctx* c, uint32_t wb, uint32_t wl, int type, const Knobs
   const uint64_t cap = a.delta ? 16ull * c->g.V + 64 : (uint64_t)c->g.V + 2;
   a.maxit = c->maxit ? c->maxit : (uint32_t)std::min<uint64_t>(cap, 0xFFFFFFF0ull);
   a.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
-  if (c->g.irp && c->pull_pct) {
+  if (c->g.ifd && c->pull_pct) {
     const uint64_t all_units = (uint64_t)c->g.V + (c->g.E >> kn.solve_cs);
     a.pull_units = (uint32_t)std::max<uint64_t>(1, all_units * c->pull_pct / 100);
     a.push_verts = (uint32_t)std::max<uint64_t>(1, (uint64_t)c->g.V * c->pull_pct / 100);
@@ -391,51 +391,43 @@ svv_status svv_load(svv_ctx* c, uint32_t V, uint64_t E, uint32_t S, const uint64
     }
   }
 
-  // transposed graph: in-edges per target, all-snapshot ones first
-  const uint32_t pull_cs = 5;
-  std::vector<uint32_t> irp, infp, iunits_n;
-  std::vector<uint2> icw;
-  std::vector<uint64_t> inm;
-  std::vector<unsigned long long> iun;
+  // transposed graph, edge-flat: in-edges sorted by target (counting sort;
+  // sources ascending within a target), all-snapshot ones and partial ones
+  // (with their masks) in separate arrays
+  const uint32_t EF = E2 - NF;
+  std::vector<uint32_t> ifd, ipd;
+  std::vector<uint2> ifcw, ipcw;
+  std::vector<uint64_t> ipm;
   if (c->pull) {
-    irp.assign((size_t)V + 1, 0);
-    infp.assign((size_t)V + 1, 0);
-    for (uint32_t v = 0; v < V; ++v) {
-      const uint32_t fe = rp[v + 1] - (nfp[v + 1] - nfp[v]);
-      for (uint32_t e = rp[v]; e < rp[v + 1]; ++e) {
-        irp[cw[e].x + 1]++;
-        if (e >= fe) infp[cw[e].x + 1]++;
-      }
+    std::vector<uint32_t> pos_f((size_t)V + 1, 0), pos_p((size_t)V + 1, 0);
+    for (uint32_t u = 0; u < V; ++u) {
+      const uint32_t fe = rp[u + 1] - (nfp[u + 1] - nfp[u]);
+      for (uint32_t e = rp[u]; e < rp[u + 1]; ++e) (e < fe ? pos_f : pos_p)[cw[e].x + 1]++;
     }
     for (uint32_t v = 0; v < V; ++v) {
-      irp[v + 1] += irp[v];
-      infp[v + 1] += infp[v];
+      pos_f[v + 1] += pos_f[v];
+      pos_p[v + 1] += pos_p[v];
     }
-    icw.assign(std::max<uint32_t>(E2, 1), make_uint2(0, 0));
-    inm.assign((size_t)std::max<uint32_t>(NF, 1) * W, 0ull);
-    std::vector<uint32_t> ff((size_t)V), pf((size_t)V), pk((size_t)V);
-    for (uint32_t v = 0; v < V; ++v) {
-      ff[v] = irp[v];
-      pf[v] = irp[v + 1] - (infp[v + 1] - infp[v]);
-      pk[v] = infp[v];
-    }
+    ifd.assign(std::max<uint32_t>(EF, 1), 0u);
+    ifcw.assign(std::max<uint32_t>(EF, 1), make_uint2(0, 0));
+    ipd.assign(std::max<uint32_t>(NF, 1), 0u);
+    ipcw.assign(std::max<uint32_t>(NF, 1), make_uint2(0, 0));
+    ipm.assign((size_t)std::max<uint32_t>(NF, 1) * W, 0ull);
     for (uint32_t u = 0; u < V; ++u) {
       const uint32_t fe = rp[u + 1] - (nfp[u + 1] - nfp[u]);
       for (uint32_t e = rp[u]; e < rp[u + 1]; ++e) {
         const uint32_t x = cw[e].x;
         if (e < fe) {
-          icw[ff[x]++] = make_uint2(u, cw[e].y);
+          const uint32_t i2 = pos_f[x]++;
+          ifd[i2] = x;
+          ifcw[i2] = make_uint2(u, cw[e].y);
         } else {
-          icw[pf[x]++] = make_uint2(u, cw[e].y);
-          const uint32_t k = pk[x]++;
-          for (uint32_t j = 0; j < W; ++j) inm[(size_t)k * W + j] = nfm[(size_t)(nfp[u] + (e - fe)) * W + j];
+          const uint32_t k = pos_p[x]++;
+          ipd[k] = x;
+          ipcw[k] = make_uint2(u, cw[e].y);
+          for (uint32_t w = 0; w < W; ++w) ipm[(size_t)k * W + w] = nfm[(size_t)(nfp[u] + (e - fe)) * W + w];
         }
       }
-    }
-    for (uint32_t v = 0; v < V; ++v) {
-      const uint32_t d = irp[v + 1] - irp[v];
-      for (uint32_t ch = 0; ch < ((d + (1u << pull_cs) - 1) >> pull_cs); ++ch)
-        iun.push_back((unsigned long long)v | ((unsigned long long)ch << 32));
     }
   }
 
@@ -482,36 +474,31 @@ svv_status svv_load(svv_ctx* c, uint32_t V, uint64_t E, uint32_t S, const uint64
   g.nfsrc = d_nfsrc;
   g.nfcw = d_nfcw;
   if (c->pull) {
-    uint32_t *d_irp, *d_infp;
-    uint2* d_icw;
-    uint64_t* d_inm;
-    unsigned long long* d_iun;
-    if ((st = alloc_n(c, c->graph_bufs, (uint64_t)V + 1, &d_irp)) ||
-        (st = alloc_n(c, c->graph_bufs, (uint64_t)V + 1, &d_infp)) ||
-        (st = alloc_n(c, c->graph_bufs, std::max<uint32_t>(E2, 1), &d_icw)) ||
-        (st = alloc_n(c, c->graph_bufs, (uint64_t)std::max<uint32_t>(NF, 1) * W, &d_inm)) ||
-        (st = alloc_n(c, c->graph_bufs, std::max<uint64_t>(iun.size(), 1), &d_iun))) {
+    uint32_t *d_ifd, *d_ipd;
+    uint2 *d_ifcw, *d_ipcw;
+    uint64_t* d_ipm;
+    if ((st = alloc_n(c, c->graph_bufs, std::max<uint32_t>(EF, 1), &d_ifd)) ||
+        (st = alloc_n(c, c->graph_bufs, std::max<uint32_t>(EF, 1), &d_ifcw)) ||
+        (st = alloc_n(c, c->graph_bufs, std::max<uint32_t>(NF, 1), &d_ipd)) ||
+        (st = alloc_n(c, c->graph_bufs, std::max<uint32_t>(NF, 1), &d_ipcw)) ||
+        (st = alloc_n(c, c->graph_bufs, (uint64_t)std::max<uint32_t>(NF, 1) * W, &d_ipm))) {
       free_graph(c);
       return st;
     }
-    cudaError_t e2 = cudaMemcpy(d_irp, irp.data(), irp.size() * 4, cudaMemcpyHostToDevice);
-    if (e2 == cudaSuccess) e2 = cudaMemcpy(d_infp, infp.data(), infp.size() * 4, cudaMemcpyHostToDevice);
-    if (e2 == cudaSuccess) e2 = cudaMemcpy(d_icw, icw.data(), (size_t)E2 * 8, cudaMemcpyHostToDevice);
-    if (e2 == cudaSuccess) e2 = cudaMemcpy(d_inm, inm.data(), (size_t)NF * W * 8, cudaMemcpyHostToDevice);
-    if (e2 == cudaSuccess && !iun.empty())
-      e2 = cudaMemcpy(d_iun, iun.data(), iun.size() * 8, cudaMemcpyHostToDevice);
-
+    cudaError_t e2 = cudaMemcpy(d_ifd, ifd.data(), (size_t)EF * 4, cudaMemcpyHostToDevice);
+    if (e2 == cudaSuccess) e2 = cudaMemcpy(d_ifcw, ifcw.data(), (size_t)EF * 8, cudaMemcpyHostToDevice);
+    if (e2 == cudaSuccess) e2 = cudaMemcpy(d_ipd, ipd.data(), (size_t)NF * 4, cudaMemcpyHostToDevice);
+    if (e2 == cudaSuccess) e2 = cudaMemcpy(d_ipcw, ipcw.data(), (size_t)NF * 8, cudaMemcpyHostToDevice);
+    if (e2 == cudaSuccess) e2 = cudaMemcpy(d_ipm, ipm.data(), (size_t)NF * W * 8, cudaMemcpyHostToDevice);
     if (e2 != cudaSuccess) {
       free_graph(c);
       return cuda_fail(c, e2, "uploading the transposed graph");
     }
-    g.irp = d_irp;
-    g.infp = d_infp;
-    g.icw = d_icw;
-    g.inmask = d_inm;
-    g.iunits = d_iun;
-    g.NIU = (uint32_t)iun.size();
-    g.pull_cs = pull_cs;
+    g.ifd = d_ifd;
+    g.ifcw = d_ifcw;
+    g.ipd = d_ipd;
+    g.ipcw = d_ipcw;
+    g.ipmask = d_ipm;
   }
 
   // scratch sized from V and E

@@ -163,7 +163,7 @@ BatchArgs batch_args(svv_ctx* c) {
   b.maxit = c->maxit;
   b.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
   b.skip_same = c->skip_same ? 1u : 0u;
-  if (c->g.irp && c->pull_pct) {
+  if (c->g.ifd && c->pull_pct) {
     const uint64_t all_units = (uint64_t)c->g.V + (c->g.E >> c->solve_cs);
     b.pull_units = (uint32_t)std::max<uint64_t>(1, all_units * c->pull_pct / 100);
     b.push_verts = (uint32_t)std::max<uint64_t>(1, (uint64_t)c->g.V * c->pull_pct / 100);

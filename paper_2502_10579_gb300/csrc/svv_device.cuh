@@ -15,6 +15,13 @@ constexpr unsigned kFullMask = 0xFFFFFFFFu;
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned long long ld_cg(const unsigned long long* p) { return __ldcg(p); }
 
+// Plain (L1-cacheable) load of a value another CTA may write in the same
+// round.  Values only improve, so a stale read can only give a worse
+// candidate, and the writer's change puts its vertex in the next frontier;
+// across rounds the team barrier's acquire orders these loads after every
+// write of the earlier rounds.
+__device__ __forceinline__ uint32_t ld_val(const uint32_t* p) { return *p; }
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

@@ -51,17 +51,16 @@ struct DevGraph {
   const uint64_t* nfmask;   // [NF*W]
   const uint32_t* nfsrc;    // [NF]
   const uint2* nfcw;        // [NF]
-  // Transposed graph for pull rounds (may be absent: irp == nullptr).  Row v
-  // holds v's in-edges (source, weight), those present in all S snapshots
-  // first; the others have W mask words at inmask[(infp[v]+j)*W].  iunits
-  // lists every (vertex, chunk of 2^pull_cs in-edges) once.
-  const uint32_t* irp;      // [V+1]
-  const uint32_t* infp;     // [V+1]
-  const uint2* icw;         // [E]
-  const uint64_t* inmask;   // [NF*W]
-  const unsigned long long* iunits;
-  uint32_t NIU;
-  uint32_t pull_cs;
+  // Transposed graph for pull rounds, edge-flat (may be absent: ifd ==
+  // nullptr).  The E-NF in-edges present in all S snapshots, sorted by
+  // target: ifd[i] is the target, ifcw[i] (source, weight).  The NF partial
+  // in-edges, sorted by target, in their own arrays with W mask words each
+  // at ipmask[k*W].  A pull pass streams both with no row lookups.
+  const uint32_t* ifd;      // [E-NF]
+  const uint2* ifcw;        // [E-NF]
+  const uint32_t* ipd;      // [NF]
+  const uint2* ipcw;        // [NF]
+  const uint64_t* ipmask;   // [NF*W]
 };
 
 struct Window {

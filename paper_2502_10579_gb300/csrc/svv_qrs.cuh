@@ -84,10 +84,10 @@ __device__ void qrs_walk(const QrsArgs& a, const Team& t, uint32_t NU, unsigned*
     const uint32_t ui = t0 + lane;
     uint32_t r = 0, beg = 0, cnt = 0, fe = 0, nfb = 0;
     if (lane < tk && ui < NU) {
-      const unsigned long long u = ld_cg(a.units + ui);
+      const unsigned long long u = a.units[ui];  // earlier phases: ordered by the barrier
       r = (uint32_t)u;
       const uint32_t ch = (uint32_t)(u >> 32);
-      const uint32_t v = ld_cg(a.uv + r);
+      const uint32_t v = a.uv[r];
       const uint32_t r0 = __ldg(g.rp + v), r1 = __ldg(g.rp + v + 1);
       const uint32_t nf0 = __ldg(g.nfp + v), nf1 = __ldg(g.nfp + v + 1);
       fe = r1 - (nf1 - nf0);
@@ -113,7 +113,7 @@ __device__ void qrs_walk(const QrsArgs& a, const Team& t, uint32_t NU, unsigned*
       if (p < total) {
         const uint32_t e = bk + (p - (ik - ck));
         const uint2 ew = __ldg(g.cw + e);
-        rx = ld_cg(a.row + ew.x);
+        rx = a.row[ew.x];
         w = ew.y;
         if (rx != kNone) {
           if (e < fk) {

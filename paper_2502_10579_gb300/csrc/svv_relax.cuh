@@ -70,7 +70,7 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           want[h] = j[h] >= 0 && mask_bit(em[h], snap0 + i);
-          curv[h] = want[h] ? ld_cg(a.val + ((size_t)ex[h] << lps) + i) : 0u;
+          curv[h] = want[h] ? ld_val(a.val + ((size_t)ex[h] << lps) + i) : 0u;
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -131,7 +131,7 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
 #pragma unroll
       for (int kk = 0; kk < K; ++kk) sv[kk] = Op::kIdentity;
       if (ui < n) {
-        const unsigned long long u = ld_cg(qin + ui);
+        const unsigned long long u = qin[ui];  // written before the last barrier
         const uint32_t r = (uint32_t)u, ch = (uint32_t)(u >> 32);
         const uint4 d = a.qrow[r];
         beg = d.x + (ch << a.cshift);
@@ -140,7 +140,7 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
         nfb = d.z;
         const uint32_t* src = a.val + ((size_t)r << lps) + gl;
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) sv[kk] = ld_cg(src + kk * P);
+        for (int kk = 0; kk < K; ++kk) sv[kk] = ld_val(src + kk * P);
       }
       const uint32_t cnt = end > beg ? end - beg : 0u;
       const uint32_t maxcnt = __reduce_max_sync(kFullMask, cnt);
@@ -189,7 +189,7 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
               const uint32_t i = gl + kk * P;
               const bool bit = (i < 64u) ? ((em0[h] >> i) & 1ull) : ((em1[h] >> (i - 64u)) & 1ull);
               want[h][kk] = ev[h] && i < a.ls && bit;
-              curv[h][kk] = want[h][kk] ? ld_cg(row + kk * P) : 0u;
+              curv[h][kk] = want[h][kk] ? ld_val(row + kk * P) : 0u;
             }
           }
           bool imp[H];

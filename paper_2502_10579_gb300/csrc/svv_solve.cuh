@@ -107,7 +107,7 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
     // large frontier is pulled: every vertex takes the best candidate over
     // its in-edges (no queue, one atomic per chunk); a small one is pushed.
     const bool dense = cta_read(&c->aux[3 + cur]) != 0u;
-    const bool can_pull = g.irp != nullptr && a.pull_units != 0u;
+    const bool can_pull = g.ifd != nullptr && a.pull_units != 0u;
     const bool pull = can_pull && (dense ? (n > a.push_verts) : (n > a.pull_units));
     if (gtid == 0) {
       atomicExch(&c->qn[clr], 0u);
@@ -122,92 +122,76 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
     const uint32_t stamp_next = it + 1u;
 
     if (pull) {
-      // ---- pull round over the transposed graph
-      uint32_t changed = 0;
-      const uint32_t pcs = g.pull_cs;
+      // ---- pull round: one pass over every in-edge, edge-flat.  A warp
+      // takes 128 consecutive in-edges (4 per lane, all loads issued before
+      // any reduction); lanes with the same target fold their candidates and
+      // the lowest of them updates the target.
+      uint32_t changed = 0, scanned = 0;
       // BFS from the source: round `it` sets level `it` exactly when it only
       // takes in-neighbours of level it-1; then every level already set is
-      // final and a visited vertex skips its in-edges (bottom-up BFS)
+      // final and a visited target skips its in-edges (bottom-up BFS)
       const bool bottom_up = Op::kLevels && a.init == kInitSource;
-      const Batches bp{g.NIU, batch_size(g.NIU, nwarps, 32u), nwarps, gwarp, &c->ticket[cur]};
-      for (uint32_t t0 = bp.first(); t0 < g.NIU; t0 = bp.next(lane)) {
-        const uint32_t ui = t0 + lane;
-        uint32_t v = 0, beg = 0, cnt = 0, fe = 0, nfb = 0;
-        if (lane < bp.tk && ui < g.NIU) {
-          const unsigned long long u = __ldg(g.iunits + ui);
-          v = (uint32_t)u;
-          const uint32_t ch = (uint32_t)(u >> 32);
-          const uint32_t r0 = __ldg(g.irp + v), r1 = __ldg(g.irp + v + 1);
-          const uint32_t nf0 = __ldg(g.infp + v), nf1 = __ldg(g.infp + v + 1);
-          fe = r1 - (nf1 - nf0);
-          nfb = nf0;
-          beg = r0 + (ch << pcs);
-          uint32_t end = min(r1, beg + (1u << pcs));
-          if (PRED == kPredAll && a.skip_nf) end = min(end, fe);
-          cnt = end > beg ? end - beg : 0u;
-          if (bottom_up && cnt && ld_cg(a.val + v) != kInf) cnt = 0;
+      const uint32_t EF = g.E - g.NF;
+      const uint32_t ntot = EF + ((PRED == kPredAll && a.skip_nf) ? 0u : g.NF);
+      const uint32_t nchunks = (ntot + 127u) >> 7;
+      for (uint32_t ch = gwarp; ch < nchunks; ch += nwarps) {
+        uint32_t d[4], src[4], w[4];
+        bool live[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t idx = (ch << 7) + 32u * j + lane;
+          live[j] = idx < ntot;
+          d[j] = 0xFFFFFFFFu - lane;  // unique per lane when not live
+          src[j] = 0;
+          w[j] = 0;
+          if (live[j]) d[j] = idx < EF ? __ldg(g.ifd + idx) : __ldg(g.ipd + (idx - EF));
         }
-        const uint32_t incl = warp_incl_scan(cnt, lane);
-        const uint32_t total = __shfl_sync(kFullMask, incl, 31);
-        if (lane == 0) relaxed += total;
-        // two 32-edge steps per iteration: both gathers are issued before
-        // either reduction
-        for (uint32_t p0 = 0; p0 < total; p0 += 64u) {
-          int kk[2];
-          uint32_t vk[2], srcv[2], ww[2];
-          bool live[2];
 #pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            const uint32_t p = p0 + 32u * j + lane;
-            kk[j] = warp_owner(incl, p < total ? p : total - 1u);
-            const int k = kk[j];
-            const uint32_t ik = __shfl_sync(kFullMask, incl, k);
-            const uint32_t ck = __shfl_sync(kFullMask, cnt, k);
-            const uint32_t bk = __shfl_sync(kFullMask, beg, k);
-            const uint32_t fk = __shfl_sync(kFullMask, fe, k);
-            const uint32_t nk = __shfl_sync(kFullMask, nfb, k);
-            vk[j] = __shfl_sync(kFullMask, v, k);
-            live[j] = false;
-            srcv[j] = 0;
-            ww[j] = 0;
-            if (p < total) {
-              const uint32_t e = bk + (p - (ik - ck));
-              const uint2 ew = __ldg(g.icw + e);
-              bool present = true;
-              if (e >= fk) {
-                const uint64_t* m = g.inmask + (size_t)(nk + (e - fk)) * g.W;
-                if (PRED == kPredAll) present = window_all(m, a.win);
-                else if (PRED == kPredAny) present = window_any(m, a.win);
-                else present = mask_bit(m, a.bit);
-              }
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t idx = (ch << 7) + 32u * j + lane;
+          if (live[j] && bottom_up && ld_val(a.val + d[j]) != kInf) live[j] = false;
+          if (live[j]) {
+            if (idx < EF) {
+              const uint2 sw = __ldg(g.ifcw + idx);
+              src[j] = sw.x;
+              w[j] = sw.y;
+            } else {
+              const uint32_t k = idx - EF;
+              const uint64_t* m = g.ipmask + (size_t)k * g.W;
+              bool present;
+              if (PRED == kPredAll) present = window_all(m, a.win);
+              else if (PRED == kPredAny) present = window_any(m, a.win);
+              else present = mask_bit(m, a.bit);
+              const uint2 sw = __ldg(g.ipcw + k);
+              src[j] = sw.x;
+              w[j] = sw.y;
               live[j] = present;
-              srcv[j] = ew.x;
-              ww[j] = ew.y;
             }
           }
-          uint32_t cand[2];
+        }
+        uint32_t cand[4];
 #pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            cand[j] = Op::kIdentity;
-            if (live[j]) {
-              const uint32_t su = ld_cg(a.val + srcv[j]);
-              if (!bottom_up || su < it) cand[j] = Op::relax(su, ww[j]);
-            }
+        for (int j = 0; j < 4; ++j) {
+          cand[j] = Op::kIdentity;
+          if (live[j]) {
+            const uint32_t su = ld_val(a.val + src[j]);
+            if (!bottom_up || su < it) cand[j] = Op::relax(su, w[j]);
           }
+          scanned += __popc(__ballot_sync(kFullMask, live[j]));
+        }
 #pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            const uint32_t p = p0 + 32u * j + lane;
-            // best candidate per target among the lanes of this step
-            const unsigned grp = __match_any_sync(kFullMask, p < total ? (uint32_t)kk[j] : 64u + lane);
-            const uint32_t best =
-                Op::better(0u, 1u) ? __reduce_min_sync(grp, cand[j]) : __reduce_max_sync(grp, cand[j]);
-            if (p < total && lane == (unsigned)(__ffs(grp) - 1) && Op::better(best, ld_cg(a.val + vk[j]))) {
-              const uint32_t old = Op::atomic(a.val + vk[j], best);
-              if (Op::better(best, old) && atomicExch(a.stamp + vk[j], stamp_next) != stamp_next) ++changed;
-            }
+        for (int j = 0; j < 4; ++j) {
+          const unsigned grp = __match_any_sync(kFullMask, d[j]);
+          const uint32_t best =
+              Op::better(0u, 1u) ? __reduce_min_sync(grp, cand[j]) : __reduce_max_sync(grp, cand[j]);
+          const uint32_t idx = (ch << 7) + 32u * j + lane;
+          if (idx < ntot && lane == (unsigned)(__ffs(grp) - 1) && Op::better(best, ld_val(a.val + d[j]))) {
+            const uint32_t old = Op::atomic(a.val + d[j], best);
+            if (Op::better(best, old) && atomicExch(a.stamp + d[j], stamp_next) != stamp_next) ++changed;
           }
         }
       }
+      if (lane == 0) relaxed += scanned;
       const uint32_t wc = __reduce_add_sync(kFullMask, changed);
       if (lane == 0 && wc) atomicAdd(qn_out, wc);
       if (!t.sync()) return false;
@@ -325,7 +309,7 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           cand[j] = Op::relax(sk[j], ew_w[j]);
-          curv[j] = act[j] ? ld_cg(a.val + x[j]) : cand[j];
+          curv[j] = act[j] ? ld_val(a.val + x[j]) : cand[j];
         }
         bool imp[2];
 #pragma unroll
