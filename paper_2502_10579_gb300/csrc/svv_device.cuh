@@ -15,6 +15,11 @@ constexpr unsigned kFullMask = 0xFFFFFFFFu;
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned long long ld_cg(const unsigned long long* p) { return __ldcg(p); }
 
+// Improvement tests.  A lane whose candidate beats the value it loaded
+// updates with a reduction (no return) and counts the target as changed: if
+// the reduction did not lower the value, another lane lowered it in the same
+// round, so the target changed in this round either way.
+//
 // Plain (L1-cacheable) load of a value another CTA may write in the same
 // round.  Values only improve, so a stale read can only give a worse
 // candidate, and the writer's change puts its vertex in the next frontier;
@@ -39,43 +44,72 @@ __device__ __forceinline__ void set_err(TeamCtl* c, uint32_t* qerr, uint32_t cod
   if (qerr) atomicCAS(qerr, 0u, code);
 }
 
+__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" : : "l"(p), "l"(v) : "memory");
+}
+
+constexpr unsigned long long kGenErr = 1ull << 63;
+
 // ---------------------------------------------------------------------------
 // Team barrier over `nblocks` co-resident CTAs (cooperative launch), with a
-// bounded wait: a CTA that waits longer than `spin_ns`, or sees an error flag
-// raised by another CTA, records the error and returns false; every caller
-// then leaves the kernel.  Sense is a generation counter.
+// bounded wait.  Arrivals are counted for the whole launch and never reset:
+// arrival number a belongs to barrier k = ceil(a / nblocks), and the CTA that
+// makes the count k * nblocks publishes k in `bar_gen` with a release store.
+// That last arriver also reads the team's error word (its acquire-release
+// add orders the read after every arrival, and so after every error set
+// before one) and publishes it in the same store, so every CTA learns of an
+// error from the one word it polls and they all leave together.  A CTA that
+// waits longer than `spin_ns`, or sees the error word set while waiting (a
+// CTA that timed out leaves without arriving), records the error and returns
+// false; every caller then leaves the kernel.
 __device__ __forceinline__ bool team_sync(TeamCtl* c, uint32_t* qerr, unsigned nblocks,
                                           unsigned long long spin_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
+    const uint32_t* ef = qerr ? qerr : &c->err;
+    const unsigned long long a = atom_add_acq_rel(&c->bar_count, 1ull) + 1ull;
+    const unsigned long long k = (a + nblocks - 1ull) / nblocks;
     int ok = 1;
-    unsigned gen = ld_acquire(&c->bar_gen);
-    __threadfence();
-    unsigned arrived = atomicAdd(&c->bar_count, 1u) + 1u;
-    if (arrived == nblocks) {
-      atomicExch(&c->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&c->bar_gen, 1u);
+    if (a == k * nblocks) {
+      const unsigned long long flag = ld_acquire(ef) != 0u ? kGenErr : 0ull;
+      st_release(&c->bar_gen, k | flag);
+      ok = flag == 0ull;
     } else {
-      unsigned long long t0 = global_ns();
-      unsigned ns = 32;
-      while (ld_acquire(&c->bar_gen) == gen) {
-        if (ld_acquire(&c->err) != 0u || (qerr && ld_acquire(qerr) != 0u)) {
-          ok = 0;
+      const unsigned long long t0 = global_ns();
+      unsigned polls = 0;
+      for (;;) {
+        const unsigned long long g = ld_acquire(&c->bar_gen);
+        if ((g & ~kGenErr) >= k) {
+          ok = (g & kGenErr) == 0ull;
           break;
         }
-        __nanosleep(ns);
-        if (ns < 256) ns <<= 1;
-        if (global_ns() - t0 > spin_ns) {
-          set_err(c, qerr, kErrTimeout);
-          ok = 0;
-          break;
+        if ((++polls & 15u) == 0u) {
+          if (ld_acquire(ef) != 0u) {
+            ok = 0;
+            break;
+          }
+          if (global_ns() - t0 > spin_ns) {
+            set_err(c, qerr, kErrTimeout);
+            ok = 0;
+            break;
+          }
         }
+        if (polls > 64u) __nanosleep(64);
       }
     }
-    __threadfence();
-    if (ok && (ld_acquire(&c->err) != 0u || (qerr && ld_acquire(qerr) != 0u))) ok = 0;
     s_ok = ok;
   }
   __syncthreads();
@@ -162,6 +196,7 @@ struct OpSSSP {  // CASMIN(Val(v), Val(u) + w), saturating
   }
   __device__ __forceinline__ static bool better(uint32_t a, uint32_t b) { return a < b; }
   __device__ __forceinline__ static uint32_t atomic(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
+  __device__ __forceinline__ static void red(uint32_t* p, uint32_t v) { atomicMin(p, v); }  // no return: a reduction
 };
 
 struct OpSSWP {  // CASMAX(Val(v), min(Val(u), w))
@@ -171,6 +206,7 @@ struct OpSSWP {  // CASMAX(Val(v), min(Val(u), w))
   __device__ __forceinline__ static uint32_t relax(uint32_t sv, uint32_t w) { return sv < w ? sv : w; }
   __device__ __forceinline__ static bool better(uint32_t a, uint32_t b) { return a > b; }
   __device__ __forceinline__ static uint32_t atomic(uint32_t* p, uint32_t v) { return atomicMax(p, v); }
+  __device__ __forceinline__ static void red(uint32_t* p, uint32_t v) { atomicMax(p, v); }  // no return: a reduction
 };
 
 struct OpBFS {  // CASMIN(Val(v), Val(u) + 1)
@@ -180,6 +216,7 @@ struct OpBFS {  // CASMIN(Val(v), Val(u) + 1)
   __device__ __forceinline__ static uint32_t relax(uint32_t sv, uint32_t) { return sv == kInf ? kInf : sv + 1; }
   __device__ __forceinline__ static bool better(uint32_t a, uint32_t b) { return a < b; }
   __device__ __forceinline__ static uint32_t atomic(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
+  __device__ __forceinline__ static void red(uint32_t* p, uint32_t v) { atomicMin(p, v); }  // no return: a reduction
 };
 
 struct OpSSNP {  // CASMIN(Val(v), max(Val(u), w))
@@ -191,6 +228,7 @@ struct OpSSNP {  // CASMIN(Val(v), max(Val(u), w))
   }
   __device__ __forceinline__ static bool better(uint32_t a, uint32_t b) { return a < b; }
   __device__ __forceinline__ static uint32_t atomic(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
+  __device__ __forceinline__ static void red(uint32_t* p, uint32_t v) { atomicMin(p, v); }  // no return: a reduction
 };
 
 // ---------------------------------------------------------------------------

@@ -20,10 +20,10 @@ enum Init : int { kInitSource = 0, kInitSeed = 1 };
 // it).  Fields live on separate 128-byte lines so the barrier counter does not
 // share a line with the counters that every warp hits.
 struct alignas(128) TeamCtl {
-  unsigned int bar_count;
-  unsigned int pad0[31];
-  unsigned int bar_gen;
-  unsigned int pad1[31];
+  unsigned long long bar_count;  // arrivals since launch (never reset)
+  unsigned int pad0[30];
+  unsigned long long bar_gen;    // last released barrier | kGenErr
+  unsigned int pad1[30];
   unsigned int qn[3];      // frontier sizes, a ring over rounds
   unsigned int pad2[29];
   unsigned int ticket[3];  // work tickets, a ring over rounds

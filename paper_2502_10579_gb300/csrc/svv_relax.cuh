@@ -75,8 +75,8 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (want[h] && Op::better(ec[h], curv[h])) {
-            const uint32_t old = Op::atomic(a.val + ((size_t)ex[h] << lps) + i, ec[h]);
-            imp[h] |= Op::better(ec[h], old);
+            Op::red(a.val + ((size_t)ex[h] << lps) + i, ec[h]);
+            imp[h] = true;
           }
         }
       }
@@ -85,10 +85,12 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
         const bool any_imp = __any_sync(kFullMask, imp[h]);
         bool push = false;
         uint32_t deg = 0;
-        if (any_imp && lane == 0 && atomicExch(a.stamp + ex[h], 1u) != 1u) {
-          push = true;
+        if (any_imp && lane == 0) {
           const uint4 d = a.qrow[ex[h]];
-          deg = d.w - d.x;
+          if (atomicExch(a.stamp + ex[h], 1u) != 1u) {
+            push = true;
+            deg = d.w - d.x;
+          }
         }
         stage_push_units(push, ex[h], deg, a.cshift, st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
       }
@@ -202,8 +204,8 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
               if (want[h][kk]) {
                 const uint32_t cand = Op::relax(sv[kk], ewt[h]);
                 if (Op::better(cand, curv[h][kk])) {
-                  const uint32_t old = Op::atomic(row + kk * P, cand);
-                  imp[h] |= Op::better(cand, old);
+                  Op::red(row + kk * P, cand);
+                  imp[h] = true;
                 }
               }
             }
@@ -219,10 +221,12 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
         }
         bool push = false;
         uint32_t deg = 0;
-        if (pend && atomicExch(a.stamp + pend_x, stamp_next) != stamp_next) {
-          push = true;
-          const uint4 d = a.qrow[pend_x];
-          deg = d.w - d.x;
+        if (pend) {
+          const uint4 d = a.qrow[pend_x];  // issued alongside the stamp exchange
+          if (atomicExch(a.stamp + pend_x, stamp_next) != stamp_next) {
+            push = true;
+            deg = d.w - d.x;
+          }
         }
         stage_push_units(push, pend_x, deg, a.cshift, st, qout, qn_out, a.qcap, c, a.qerr, lane);
       }

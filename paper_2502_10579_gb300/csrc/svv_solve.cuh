@@ -71,12 +71,13 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
           const uint32_t u = __ldg(g.nfsrc + k);
           const uint2 e = __ldg(g.nfcw + k);
           x = e.x;
-          cand = Op::relax(ld_cg(a.val + u), e.y);
-          if (Op::better(cand, ld_cg(a.val + x))) {
-            const uint32_t old = Op::atomic(a.val + x, cand);
-            if (Op::better(cand, old) && atomicExch(a.stamp + x, 1u) != 1u) {
+          cand = Op::relax(ld_val(a.val + u), e.y);
+          if (Op::better(cand, ld_val(a.val + x))) {
+            Op::red(a.val + x, cand);
+            const uint32_t r0 = __ldg(g.rp + x), r1 = __ldg(g.rp + x + 1);
+            if (atomicExch(a.stamp + x, 1u) != 1u) {
               push = true;
-              deg = g.rp[x + 1] - g.rp[x];
+              deg = r1 - r0;
             }
           }
         }
@@ -186,8 +187,8 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
               Op::better(0u, 1u) ? __reduce_min_sync(grp, cand[j]) : __reduce_max_sync(grp, cand[j]);
           const uint32_t idx = (ch << 7) + 32u * j + lane;
           if (idx < ntot && lane == (unsigned)(__ffs(grp) - 1) && Op::better(best, ld_val(a.val + d[j]))) {
-            const uint32_t old = Op::atomic(a.val + d[j], best);
-            if (Op::better(best, old) && atomicExch(a.stamp + d[j], stamp_next) != stamp_next) ++changed;
+            Op::red(a.val + d[j], best);
+            if (atomicExch(a.stamp + d[j], stamp_next) != stamp_next) ++changed;
           }
         }
       }
@@ -314,17 +315,17 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
         bool imp[2];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          imp[j] = false;
-          if (act[j] && Op::better(cand[j], curv[j])) {
-            const uint32_t old = Op::atomic(a.val + x[j], cand[j]);
-            imp[j] = Op::better(cand[j], old);
-          }
+          imp[j] = act[j] && Op::better(cand[j], curv[j]);
+          if (imp[j]) Op::red(a.val + x[j], cand[j]);
         }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          if (imp[j] && atomicExch(a.stamp + x[j], stamp_next) != stamp_next) {
-            push[j] = true;
-            deg[j] = __ldg(g.rp + x[j] + 1) - __ldg(g.rp + x[j]);
+          if (imp[j]) {
+            const uint32_t r0 = __ldg(g.rp + x[j]), r1 = __ldg(g.rp + x[j] + 1);
+            if (atomicExch(a.stamp + x[j], stamp_next) != stamp_next) {
+              push[j] = true;
+              deg[j] = r1 - r0;
+            }
           }
         }
         stage_push_units(push[0], x[0], deg[0], a.cshift, st, qout, qn_out, a.qcap, c, a.qerr, lane);
