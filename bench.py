@@ -270,11 +270,17 @@ def run_reference(args, world, rank):
 def _setup_ctx(svv, log, dev, args):
     rp, col, w, mask = svv.svv_build_versioned_csr(log.V, log.S, log.src, log.dst, log.w, log.t_add, log.t_del)
     ctx = svv.Context(dev)
+    _tune(ctx, args)
     ctx.load_csr(log.V, log.S, rp, col, w, mask)
+    return ctx
+
+
+def _tune(ctx, args):
+    """--tune knobs, set before the graph is loaded (chunk sizes and the
+    transposed graph are fixed at load)."""
     for kv in args.tune:
         k, v = kv.split("=", 1)
         ctx.set_tuning(k, int(v))
-    return ctx
 
 
 def _clocks_start(rank, args, dev):
@@ -516,11 +522,9 @@ def main():
     rp, col, w, mask = svv.svv_build_versioned_csr(log.V, log.S, log.src, log.dst, log.w, log.t_add, log.t_del)
     gc = graph_counts(log, rp, mask)
     ctx = svv.Context(dev)
+    _tune(ctx, args)
     ctx.load_csr(log.V, log.S, rp, col, w, mask)
     ctx.set_tuning("phase_timing", 1)
-    for kv in args.tune:
-        k, v = kv.split("=", 1)
-        ctx.set_tuning(k, int(v))
     outs = [ctx.empty_out(q.win_len) for q in qs]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=f"cuda:{dev}")
     stream = torch.cuda.current_stream(dev)

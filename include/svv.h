@@ -304,7 +304,8 @@ svv_status svv_autotune(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t w
 /* Tuning knobs, by name: "max_iters" (frontier-round cap per solve, 0 = V+2),
  * "spin_limit_ms" (bound on every device-side wait, default 1000),
  * "solve_chunk" / "relax_chunk" / "qrs_chunk" (edges per work unit, powers of
- * two), "blocks_per_sm" (0 = occupancy limit), "delta_sssp" / "delta_sswp"
+ * two; defaults 32 / 16 / 32; a chunk smaller than the one the graph was
+ * loaded with must be set before svv_load), "blocks_per_sm" (0 = occupancy limit), "delta_sssp" / "delta_sswp"
  * (near-far width of the SSSP / SSWP solves: a frontier round relaxes only the
  * vertices within this distance of the round's best value and keeps the rest
  * queued; 0 relaxes every queued vertex; results are identical either way),

@@ -110,7 +110,7 @@ struct svv_ctx {
   // tuning
   uint32_t maxit = 0;
   uint32_t spin_ms = 1000;
-  uint32_t solve_cs = 5, relax_cs = 5, qrs_cs = 5;
+  uint32_t solve_cs = 5, relax_cs = 4, qrs_cs = 5;
   uint32_t delta[3] = {0, 0, 0};  // near-far width per query type (0 = off)
   int bps = 0;
   int threads = 512;

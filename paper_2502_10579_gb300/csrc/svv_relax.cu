@@ -36,36 +36,41 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) relax_kernel(RelaxArgs a) {
 // Output scatter: out[(s0+i)*V + v] = intersection value if v is stable, else
 // the relaxed value of its row.  A CTA stages a tile of kTV vertices x ls
 // snapshots in shared memory so the row reads and the snapshot-major writes
-// both coalesce; when V is a multiple of 4 the writes are 16-byte streaming
-// stores (the output is not read again by this query).
-constexpr int kTV = 64;
+// both coalesce.  The tile is filled with every load independent of the
+// others (the tile's row map first, then all relaxed rows at once, a warp per
+// 32 consecutive snapshots of one row), so a CTA waits for two memory round
+// trips, not one per vertex.  When V is a multiple of 4 the writes are
+// 16-byte streaming stores (the output is not read again by this query).
+constexpr int kTV = 128;
 constexpr int kTVP = kTV + 4;  // padded tile row: keeps 16-byte alignment
 constexpr int kScatterThreads = 256;
 
 __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(ScatterArgs a) {
   extern __shared__ __align__(16) uint32_t tile[];  // [ls][kTVP]
+  __shared__ uint32_t s_row[kTV], s_x[kTV];
   if (*a.qerr != 0u) return;
-  const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t v0 = blockIdx.x * kTV;
+  const uint32_t nv = min((uint32_t)kTV, a.V - v0);
   const uint32_t lps = __ffs(a.LP) - 1;
-  for (uint32_t t = wid; t < (uint32_t)kTV; t += nw) {
-    const uint32_t v = v0 + t;
-    if (v >= a.V) break;
-    const uint32_t r = a.row[v];
-    if (r == kNone) {
-      const uint32_t x = a.rI[v];
-      for (uint32_t i = lane; i < a.ls; i += 32u) tile[i * kTVP + t] = x;
-    } else {
-      const uint32_t* src = a.val + ((size_t)r << lps);
-      for (uint32_t i = lane; i < a.ls; i += 32u) tile[i * kTVP + t] = src[i];
-    }
+  for (uint32_t t = threadIdx.x; t < (uint32_t)kTV; t += blockDim.x) {
+    const bool in = t < nv;
+    s_row[t] = in ? a.row[v0 + t] : kNone;
+    s_x[t] = in ? a.rI[v0 + t] : 0u;
   }
   __syncthreads();
-  const uint32_t nv = min((uint32_t)kTV, a.V - v0);
+  // idx = t * ls + i: consecutive threads take consecutive snapshots of a row
+  const uint32_t n = (uint32_t)kTV * a.ls;
+  for (uint32_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const uint32_t t = idx / a.ls, i = idx - t * a.ls;
+    const uint32_t r = s_row[t];
+    tile[i * kTVP + t] = r == kNone ? s_x[t] : a.val[((size_t)r << lps) + i];
+  }
+  __syncthreads();
   if ((a.V & 3u) == 0u && nv == (uint32_t)kTV && ((uintptr_t)a.out & 15u) == 0u) {
-    // 16 threads x 16 bytes per tile row, 16 rows per pass
-    const uint32_t q = threadIdx.x & 15u, r0 = threadIdx.x >> 4;
-    for (uint32_t i = r0; i < a.ls; i += kScatterThreads / 16) {
+    // a warp per tile row: 32 threads x 16 bytes
+    constexpr uint32_t kQ = kTV / 4, kRows = kScatterThreads / kQ;
+    const uint32_t q = threadIdx.x % kQ, r0 = threadIdx.x / kQ;
+    for (uint32_t i = r0; i < a.ls; i += kRows) {
       const uint4 x = *reinterpret_cast<const uint4*>(tile + i * kTVP + 4 * q);
       __stcs(reinterpret_cast<uint4*>(a.out + (size_t)(a.s0 + i) * a.V + v0) + q, x);
     }
@@ -139,7 +144,12 @@ cudaError_t launch_relax(int type, uint32_t P, uint32_t K, const RelaxArgs& a, L
 
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
   const uint32_t blocks = (a.V + kTV - 1) / kTV;
-  const size_t smem = (size_t)a.ls * kTVP * sizeof(uint32_t);
+  const size_t smem = (size_t)a.ls * kTVP * sizeof(uint32_t);  // up to 66 KB at 128 snapshots
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   scatter_kernel<<<blocks, kScatterThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
