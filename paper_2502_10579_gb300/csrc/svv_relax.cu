@@ -36,19 +36,25 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) relax_kernel(RelaxArgs a) {
 // Output scatter: out[(s0+i)*V + v] = intersection value if v is stable, else
 // the relaxed value of its row.  A CTA stages a tile of kTV vertices x ls
 // snapshots in shared memory so the row reads and the snapshot-major writes
-// both coalesce.  The tile is filled with every load independent of the
-// others (the tile's row map first, then all relaxed rows at once, a warp per
-// 32 consecutive snapshots of one row), so a CTA waits for two memory round
-// trips, not one per vertex.  When V is a multiple of 4 the writes are
-// 16-byte streaming stores (the output is not read again by this query).
+// both coalesce.  The tile's row map is read first; then a warp takes four
+// vertices at a time with a lane per snapshot, every load independent of the
+// others.  Tile element (i, t) sits at i*kTV + (t ^ (i & 31)): the lanes of a
+// fill store (consecutive i, one t) hit 32 different banks, and the four
+// words of an aligned 16-byte group stay in one group, permuted by i & 3.
+// When V is a multiple of 4 the writes are 16-byte streaming stores (the
+// output is not read again by this query).
 constexpr int kTV = 128;
-constexpr int kTVP = kTV + 4;  // padded tile row: keeps 16-byte alignment
 constexpr int kScatterThreads = 256;
 
+__device__ __forceinline__ uint32_t pick4(const uint4& w, uint32_t k) {
+  return k == 0 ? w.x : k == 1 ? w.y : k == 2 ? w.z : w.w;
+}
+
 __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(ScatterArgs a) {
-  extern __shared__ __align__(16) uint32_t tile[];  // [ls][kTVP]
+  extern __shared__ __align__(16) uint32_t tile[];  // [ls][kTV], swizzled
   __shared__ uint32_t s_row[kTV], s_x[kTV];
   if (*a.qerr != 0u) return;
+  const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t v0 = blockIdx.x * kTV;
   const uint32_t nv = min((uint32_t)kTV, a.V - v0);
   const uint32_t lps = __ffs(a.LP) - 1;
@@ -58,12 +64,20 @@ __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(ScatterArgs a)
     s_x[t] = in ? a.rI[v0 + t] : 0u;
   }
   __syncthreads();
-  // idx = t * ls + i: consecutive threads take consecutive snapshots of a row
-  const uint32_t n = (uint32_t)kTV * a.ls;
-  for (uint32_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const uint32_t t = idx / a.ls, i = idx - t * a.ls;
-    const uint32_t r = s_row[t];
-    tile[i * kTVP + t] = r == kNone ? s_x[t] : a.val[((size_t)r << lps) + i];
+  for (uint32_t t0 = 4u * wid; t0 < (uint32_t)kTV; t0 += 4u * nw) {
+    uint32_t r[4], x[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      r[h] = s_row[t0 + h];
+      x[h] = s_x[t0 + h];
+    }
+    for (uint32_t i = lane; i < a.ls; i += 32u) {
+      uint32_t y[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) y[h] = r[h] == kNone ? x[h] : a.val[((size_t)r[h] << lps) + i];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) tile[i * kTV + ((t0 + h) ^ (i & 31u))] = y[h];
+    }
   }
   __syncthreads();
   if ((a.V & 3u) == 0u && nv == (uint32_t)kTV && ((uintptr_t)a.out & 15u) == 0u) {
@@ -71,14 +85,16 @@ __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(ScatterArgs a)
     constexpr uint32_t kQ = kTV / 4, kRows = kScatterThreads / kQ;
     const uint32_t q = threadIdx.x % kQ, r0 = threadIdx.x / kQ;
     for (uint32_t i = r0; i < a.ls; i += kRows) {
-      const uint4 x = *reinterpret_cast<const uint4*>(tile + i * kTVP + 4 * q);
-      __stcs(reinterpret_cast<uint4*>(a.out + (size_t)(a.s0 + i) * a.V + v0) + q, x);
+      const uint32_t sw = i & 31u;
+      const uint4 w = *reinterpret_cast<const uint4*>(tile + i * kTV + 4u * (q ^ (sw >> 2)));
+      const uint32_t k = sw & 3u;
+      const uint4 o = make_uint4(pick4(w, k), pick4(w, 1u ^ k), pick4(w, 2u ^ k), pick4(w, 3u ^ k));
+      __stcs(reinterpret_cast<uint4*>(a.out + (size_t)(a.s0 + i) * a.V + v0) + q, o);
     }
   } else {
-    for (uint32_t idx = threadIdx.x; idx < a.ls * (uint32_t)kTV; idx += blockDim.x) {
-      const uint32_t i = idx / kTV, t = idx % kTV;
-      if (t < nv) a.out[(size_t)(a.s0 + i) * a.V + v0 + t] = tile[i * kTVP + t];
-    }
+    for (uint32_t i = wid; i < a.ls; i += nw)
+      for (uint32_t t = lane; t < nv; t += 32u)
+        a.out[(size_t)(a.s0 + i) * a.V + v0 + t] = tile[i * kTV + (t ^ (i & 31u))];
   }
 }
 
@@ -144,7 +160,7 @@ cudaError_t launch_relax(int type, uint32_t P, uint32_t K, const RelaxArgs& a, L
 
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
   const uint32_t blocks = (a.V + kTV - 1) / kTV;
-  const size_t smem = (size_t)a.ls * kTVP * sizeof(uint32_t);  // up to 66 KB at 128 snapshots
+  const size_t smem = (size_t)a.ls * kTV * sizeof(uint32_t);  // up to 64 KB at 128 snapshots
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute((const void*)scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
