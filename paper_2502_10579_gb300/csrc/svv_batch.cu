@@ -43,9 +43,12 @@ __device__ uint32_t pick_instance(const BatchArgs& b) {
   unsigned ns = 256;
   for (;;) {
     const uint32_t tail = *b.live_tail;
-    const uint32_t cur = ld_acquire(b.next);
+    const uint32_t cur = ld_relaxed(b.next);  // no L1 drop per poll (other teams share the SM)
     if (cur < tail) {
-      if (atomicCAS(b.next, cur, cur + 1u) == cur) return cur;
+      if (atomicCAS(b.next, cur, cur + 1u) == cur) {
+        fence_acq_rel();
+        return cur;
+      }
       continue;
     }
     if (*b.live_stop) return kNoInst;

@@ -56,6 +56,23 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
   return v;
 }
 
+// Relaxed polls: an acquire load on every spin would also drop the SM's L1
+// lines that co-resident CTAs are still reading; one acquire fence after the
+// poll that sees the release gives the same ordering.
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" : : "l"(p), "l"(v) : "memory");
 }
@@ -91,13 +108,14 @@ __device__ __forceinline__ bool team_sync(TeamCtl* c, uint32_t* qerr, unsigned n
       const unsigned long long t0 = global_ns();
       unsigned polls = 0;
       for (;;) {
-        const unsigned long long g = ld_acquire(&c->bar_gen);
+        const unsigned long long g = ld_relaxed(&c->bar_gen);
         if ((g & ~kGenErr) >= k) {
+          fence_acq_rel();
           ok = (g & kGenErr) == 0ull;
           break;
         }
         if ((++polls & 15u) == 0u) {
-          if (ld_acquire(ef) != 0u) {
+          if (ld_relaxed(ef) != 0u) {
             ok = 0;
             break;
           }
@@ -117,14 +135,15 @@ __device__ __forceinline__ bool team_sync(TeamCtl* c, uint32_t* qerr, unsigned n
 }
 
 // ---------------------------------------------------------------------------
-// One acquire load per CTA, broadcast through shared memory: a per-round
-// counter read by every thread would send one uncached request per thread to
-// the same L2 line.
+// One load per CTA, broadcast through shared memory: a per-round counter read
+// by every thread would send one uncached request per thread to the same L2
+// line.  The counters are read after a team barrier (or at kernel start), whose
+// acquire already orders them, so the load is relaxed.
 __device__ __forceinline__ void cta_read2(const unsigned* p, const unsigned* q, uint32_t& x, uint32_t& y) {
   __shared__ uint32_t s_v[2];
   if (threadIdx.x == 0) {
-    s_v[0] = ld_acquire(p);
-    s_v[1] = q ? ld_acquire(q) : 0u;
+    s_v[0] = ld_relaxed(p);
+    s_v[1] = q ? ld_relaxed(q) : 0u;
   }
   __syncthreads();
   x = s_v[0];
