@@ -143,6 +143,10 @@ svv_status svv_query(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_
  * GPU, the instances run in order with svv_query's per-phase kernels, each
  * instance's status kept on the device and read back once at the end
  * ("batch_mode" tuning key: 0 = by graph size, 1 = one launch, 2 = in order).
+ * A spec's `out` may also be HOST memory (win_len*V uint32): the batch then
+ * runs in order, and each such result is computed into one of two device
+ * staging slots and copied back on a second stream while the next instance
+ * computes; the call returns after the last copy.
  * Each spec is checked as in svv_query; an invalid spec gets SVV_EINVAL and
  * is skipped.  Every valid spec's `out` is written as svv_query would write
  * it, and its status is set (SVV_OK, or SVV_ETIMEOUT for an instance that hit
@@ -233,8 +237,11 @@ svv_status svv_query_compact(svv_ctx *ctx, svv_type type, uint32_t source, uint3
 svv_status svv_query_plain(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
                            uint32_t win_len, uint32_t *out, void *cuda_stream);
 
-/* svv_query with `out_host` a HOST buffer of win_len*V uint32 (pinned memory
- * is fastest): the device result is copied back inside the call. */
+/* svv_query with `out_host` a HOST buffer of win_len*V uint32, complete when
+ * the call returns.  Page-locked memory the device can address (cudaHostAlloc,
+ * cudaHostRegister, torch pin_memory) is written directly by the output
+ * scatter over the host link, so the transfer overlaps the scatter; any other
+ * host memory goes through a device staging buffer and one copy. */
 svv_status svv_query_host(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
                           uint32_t win_len, uint32_t *out_host, void *cuda_stream);
 

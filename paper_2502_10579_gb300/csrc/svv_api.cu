@@ -22,6 +22,10 @@ void free_graph(svv_ctx* c) {
   free_batch(c);
   free_list(c, c->graph_bufs);
   free_list(c, c->scratch_bufs);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  free_list(c, c->bstage_bufs);
+  c->bstage[0] = c->bstage[1] = nullptr;
+  c->bstage_cap = 0;
   c->allocated = 0;
   c->loaded = false;
   c->g = DevGraph{};
@@ -209,6 +213,11 @@ void svv_destroy(svv_ctx* c) {
       if (e) cudaEventDestroy(e);
     for (auto& e : c->bev)
       if (e) cudaEventDestroy(e);
+    for (int i = 0; i < 2; ++i) {
+      if (c->ev_done[i]) cudaEventDestroy(c->ev_done[i]);
+      if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->trace) cudaFree(c->trace);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -762,26 +771,78 @@ namespace svv {
 // kernels on one stream.  Each instance's error word is copied to its own
 // device slot, and all are read back once at the end, so nothing waits on the
 // host between instances.
-svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, uint32_t* qerr_dev, uint32_t* qerr_host,
-                          cudaStream_t s, float* ms) {
-  uint32_t Lmax = 1;
-  for (uint32_t k = 0; k < m; ++k) Lmax = std::max(Lmax, inst[k].wl);
+// Two device staging slots of L*V words for host outputs (grown on demand).
+static svv_status ensure_bstage(svv_ctx* c, uint64_t words) {
+  cudaError_t e = cudaSuccess;
+  if (!c->copy_stream && (e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(c, e, "copy stream");
+  for (int i = 0; i < 2; ++i) {
+    if (!c->ev_done[i] && (e = cudaEventCreateWithFlags(&c->ev_done[i], cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(c, e, "cudaEventCreate");
+    if (!c->ev_copied[i] && (e = cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(c, e, "cudaEventCreate");
+  }
+  if (words <= c->bstage_cap) return SVV_OK;
+  cudaStreamSynchronize(c->copy_stream);
+  free_list(c, c->bstage_bufs);
+  c->allocated -= std::min<uint64_t>(c->allocated, 2 * round256(c->bstage_cap * 4));
+  c->bstage[0] = c->bstage[1] = nullptr;
+  c->bstage_cap = 0;
+  svv_status st;
+  if ((st = alloc_n(c, c->bstage_bufs, words, &c->bstage[0])) || (st = alloc_n(c, c->bstage_bufs, words, &c->bstage[1])))
+    return st;
+  c->bstage_cap = words;
+  return SVV_OK;
+}
+
+svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, const char* host_out,
+                          uint32_t* qerr_dev, uint32_t* qerr_host, cudaStream_t s, float* ms) {
+  uint32_t Lmax = 1, Lhost = 0;
+  for (uint32_t k = 0; k < m; ++k) {
+    Lmax = std::max(Lmax, inst[k].wl);
+    if (host_out && host_out[k]) Lhost = std::max(Lhost, inst[k].wl);
+  }
   svv_status st = ensure_window(c, Lmax);
   if (st) return st;
+  if (Lhost && (st = ensure_bstage(c, (uint64_t)Lhost * c->g.V))) return st;
   cudaError_t e = cudaSuccess;
   for (auto& ev : c->bev)
     if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
   cudaEventRecord(c->bev[0], s);
+  // A host output is computed into a staging slot and copied back on the copy
+  // stream while the next instance computes; a slot is reused only after its
+  // last copy has finished.
+  bool used[2] = {false, false};
+  uint32_t nh = 0;
   for (uint32_t k = 0; k < m; ++k) {
     float a = 0.f, b = 0.f;
-    if ((st = enqueue_query(c, inst[k].type, inst[k].source, inst[k].wb, inst[k].wl, inst[k].out, s, false, &a, &b)))
+    uint32_t* out = inst[k].out;
+    int slot = -1;
+    if (host_out && host_out[k]) {
+      slot = (int)(nh++ & 1u);
+      if (used[slot] && (e = cudaStreamWaitEvent(s, c->ev_copied[slot], 0)) != cudaSuccess)
+        return cuda_fail(c, e, "staging wait");
+      out = c->bstage[slot];
+    }
+    if ((st = enqueue_query(c, inst[k].type, inst[k].source, inst[k].wb, inst[k].wl, out, s, false, &a, &b)))
       return st;
     if ((e = cudaMemcpyAsync(qerr_dev + k, c->qerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       return cuda_fail(c, e, "batch status copy");
+    if (slot >= 0) {
+      const size_t bytes = (size_t)inst[k].wl * c->g.V * sizeof(uint32_t);
+      e = cudaEventRecord(c->ev_done[slot], s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->ev_done[slot], 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(inst[k].out, out, bytes, cudaMemcpyDeviceToHost, c->copy_stream);
+      if (e == cudaSuccess) e = cudaEventRecord(c->ev_copied[slot], c->copy_stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "copying a result to the host");
+      used[slot] = true;
+    }
   }
   cudaEventRecord(c->bev[1], s);
   e = cudaMemcpyAsync(qerr_host, qerr_dev, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && nh) e = cudaStreamSynchronize(c->copy_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "batch");
   *ms = 0.f;
   cudaEventElapsedTime(ms, c->bev[0], c->bev[1]);
@@ -945,6 +1006,17 @@ svv_status svv_query_host(svv_ctx* c, svv_type type, uint32_t source, uint32_t w
   svv_status st = check_query(c, (int)type, source, wb, wl, out_host);
   if (st) return st;
   DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // page-locked and mapped: the scatter writes the host buffer directly
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, out_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer != nullptr && at.device == c->device) {
+    if ((st = svv_query(c, type, source, wb, wl, static_cast<uint32_t*>(at.devicePointer), stream))) return st;
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "query into host memory");
+    return SVV_OK;
+  }
+  cudaGetLastError();  // not a registered pointer
   const uint64_t need = (uint64_t)wl * c->g.V;
   if (need > c->staging_cap) {
     if (c->staging) {
@@ -960,7 +1032,6 @@ svv_status svv_query_host(svv_ctx* c, svv_type type, uint32_t source, uint32_t w
   }
   st = svv_query(c, type, source, wb, wl, c->staging, stream);
   if (st) return st;
-  cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(out_host, c->staging, need * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "copying the result to the host");

@@ -214,13 +214,27 @@ extern "C" svv_status svv_query_batch(svv_ctx* c, uint32_t n, svv_query_spec* sp
   const uint32_t m = (uint32_t)inst.size();
   cudaStream_t s = (cudaStream_t)stream;
   svv_status st;
-  if (!batch_one_launch(c)) {
+  // outputs in host memory (page-locked or not) run in order, staged
+  std::vector<char> host_out(m, 0);
+  bool any_host = false;
+  for (uint32_t k = 0; k < m; ++k) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, inst[k].out) != cudaSuccess) {
+      cudaGetLastError();
+      at.type = cudaMemoryTypeUnregistered;
+    }
+    host_out[k] = at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+    any_host |= host_out[k] != 0;
+  }
+  if (any_host || !batch_one_launch(c)) {
     if ((st = ensure_instances(c, m))) return st;
     std::vector<uint32_t> qerr(m);
     float ms = 0.f;
     {
       ServeFence fence(c, s);
-      if ((st = batch_in_order(c, inst.data(), m, c->batch.d_qerr, qerr.data(), s, &ms))) return st;
+      if ((st = batch_in_order(c, inst.data(), m, any_host ? host_out.data() : nullptr, c->batch.d_qerr,
+                               qerr.data(), s, &ms)))
+        return st;
     }
     svv_status overall = first_bad;
     for (uint32_t k = 0; k < m; ++k) {

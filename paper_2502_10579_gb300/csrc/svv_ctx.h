@@ -149,6 +149,12 @@ struct svv_ctx {
   uint64_t valcap = 0;
   uint32_t* staging = nullptr;  // device output for svv_query_host
   uint64_t staging_cap = 0;
+  // svv_query_batch with host outputs: two staging slots and a copy stream
+  uint32_t* bstage[2] = {nullptr, nullptr};
+  uint64_t bstage_cap = 0;      // words per slot
+  std::vector<void*> bstage_bufs;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_done[2] = {}, ev_copied[2] = {};
 
   // paper's ablations (Table 3): snapshots per relaxation pass (1 = one
   // snapshot at a time, the non-concurrent mode) and stable-vertex pruning
@@ -268,7 +274,7 @@ struct ServeFence {
   ServeFence(svv_ctx* c, cudaStream_t s);
   ~ServeFence();
 };
-svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, uint32_t* qerr_dev, uint32_t* qerr_host,
-                          cudaStream_t s, float* ms);
+svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, const char* host_out,
+                          uint32_t* qerr_dev, uint32_t* qerr_host, cudaStream_t s, float* ms);
 
 }  // namespace svv

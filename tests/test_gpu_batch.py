@@ -122,3 +122,25 @@ def test_batch_config3_shape(svv):
             np.testing.assert_array_equal(svv.to_u32(o), svv.to_u32(ctx.query(t, s, b, L)))
         for (t, s, b, L), o in list(zip(specs, outs))[:3]:
             np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L))
+
+
+def test_batch_host_outputs(svv):
+    """Host outputs (page-locked and pageable) in a batch: computed into
+    staging slots and copied back while the next instance computes."""
+    log = W.scaled_rmat(scale=12, edge_factor=8, n_snapshots=70, rate=0.004, seed=23, add_mode="skewed")
+    specs = _mixed(log, 7, 31)
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        outs = []
+        for k, (t, s, b, L) in enumerate(specs):
+            if k % 3 == 0:
+                outs.append(torch.empty((L, log.V), dtype=torch.int32, pin_memory=True))
+            elif k % 3 == 1:
+                outs.append(np.empty((L, log.V), np.uint32))
+            else:
+                outs.append(ctx.empty_out(L))
+        st = svv.svv_query_batch(ctx.h, [sp + (o,) for sp, o in zip(specs, outs)])
+        assert st == [0] * len(specs)
+        for (t, s, b, L), o in zip(specs, outs):
+            got = o if isinstance(o, np.ndarray) else svv.to_u32(o) if o.is_cuda else o.numpy().view(np.uint32)
+            np.testing.assert_array_equal(got, oracle.query(log, t, s, b, L))

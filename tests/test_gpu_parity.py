@@ -188,6 +188,12 @@ def test_inputs_on_device_and_host_output(svv, small):
         host = np.empty((log.S, log.V), np.uint32)
         ctx.query_host(0, 0, 0, log.S, host)
         np.testing.assert_array_equal(host, oracle.query(log, 0, 0, 0, log.S))
+        # page-locked host memory: the scatter writes it directly
+        pinned = torch.empty((log.S, log.V), dtype=torch.int32, pin_memory=True)
+        for t in (1, 2):
+            ctx.query_host(t, 3, 1, log.S - 1, pinned[: log.S - 1].numpy())
+            np.testing.assert_array_equal(pinned[: log.S - 1].numpy().view(np.uint32),
+                                          oracle.query(log, t, 3, 1, log.S - 1))
 
 
 def test_error_paths(svv, small):
