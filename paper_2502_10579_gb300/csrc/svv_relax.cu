@@ -26,7 +26,7 @@ namespace svv {
 constexpr int kRelaxThreads = 512;
 
 template <class Op, int P, int K>
-__global__ void __launch_bounds__(kRelaxThreads, 3) relax_kernel(RelaxArgs a) {
+__global__ void __launch_bounds__(kRelaxThreads, 2) relax_kernel(RelaxArgs a) {
   __shared__ unsigned long long s_stage[(kRelaxThreads / 32) * kStageUnits];
   const Team t{a.ctl, a.qerr, gridDim.x, blockIdx.x, a.spin_ns};
   relax_team<Op, P, K>(a, t, s_stage);

@@ -31,7 +31,7 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
   if (!t.sync()) return false;
   if (a.trace && gtid == 0 && a.trace_cap) a.trace[0] = global_ns() & 0xFFFFFFFFFFull;
 
-  // ---- round 0b: seed from addition edges with an unstable sink; two
+  // ---- round 0b: seed from addition edges with an unstable sink; four
   // qualifying edges per warp iteration, lanes over the slab's snapshots
   for (uint32_t k0 = gwarp * 32u; k0 < g.NF; k0 += nwarps * 32u) {
     const uint32_t k = k0 + lane;
@@ -47,33 +47,47 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
         if (qual) cand = Op::relax(a.rI[__ldg(g.nfsrc + k)], e.y);
       }
     }
+    // the owner lane extracts the slab's presence bits once; the warp then
+    // takes four qualifying edges at a time with the bits in registers
+    uint64_t mlo = 0ull, mhi = 0ull;
+    if (qual) {
+      const uint64_t* mp = g.nfmask + (size_t)k * g.W;
+      mlo = mask_extract(mp, g.W, snap0);
+      if (a.ls > 64u) mhi = mask_extract(mp, g.W, snap0 + 64u);
+    }
     unsigned bq = __ballot_sync(kFullMask, qual);
+    constexpr int HS = 4;
     while (bq) {
-      int j[2];
-      j[0] = __ffs(bq) - 1;
-      bq &= bq - 1u;
-      j[1] = bq ? __ffs(bq) - 1 : -1;
-      if (bq) bq &= bq - 1u;
-      uint32_t ex[2], ec[2];
-      const uint64_t* em[2];
+      int j[HS];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < HS; ++h) {
+        j[h] = bq ? __ffs(bq) - 1 : -1;
+        if (bq) bq &= bq - 1u;
+      }
+      uint32_t ex[HS], ec[HS];
+      uint64_t ml[HS], mh[HS];
+#pragma unroll
+      for (int h = 0; h < HS; ++h) {
         const int src = j[h] < 0 ? j[0] : j[h];
         ex[h] = __shfl_sync(kFullMask, rx, src);
         ec[h] = __shfl_sync(kFullMask, cand, src);
-        em[h] = g.nfmask + (size_t)(k0 + src) * g.W;
+        ml[h] = __shfl_sync(kFullMask, mlo, src);
+        mh[h] = __shfl_sync(kFullMask, mhi, src);
       }
-      bool imp[2] = {false, false};
-      for (uint32_t i = lane; i < a.ls; i += 32u) {
-        bool want[2];
-        uint32_t curv[2];
+      bool imp[HS];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          want[h] = j[h] >= 0 && mask_bit(em[h], snap0 + i);
+      for (int h = 0; h < HS; ++h) imp[h] = false;
+      for (uint32_t i = lane; i < a.ls; i += 32u) {
+        bool want[HS];
+        uint32_t curv[HS];
+#pragma unroll
+        for (int h = 0; h < HS; ++h) {
+          const uint64_t bit = i < 64u ? (ml[h] >> i) : (mh[h] >> (i - 64u));
+          want[h] = j[h] >= 0 && (bit & 1ull);
           curv[h] = want[h] ? ld_val(a.val + ((size_t)ex[h] << lps) + i) : 0u;
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < HS; ++h) {
           if (want[h] && Op::better(ec[h], curv[h])) {
             Op::red(a.val + ((size_t)ex[h] << lps) + i, ec[h]);
             imp[h] = true;
@@ -81,7 +95,7 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
         }
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < HS; ++h) {
         const bool any_imp = __any_sync(kFullMask, imp[h]);
         bool push = false;
         uint32_t deg = 0;
