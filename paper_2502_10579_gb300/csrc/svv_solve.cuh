@@ -245,12 +245,6 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
         if (PRED == kPredAll && a.skip_nf) end = min(end, fe);
         cnt = end > beg ? end - beg : 0u;
         sv = ld_cg(a.val + v);
-        if (a.procv && cnt) {
-          // chunk ids v + rp[v]/C + ch are distinct across vertices
-          uint32_t* pv = a.procv + v + (r0 >> a.cshift) + ch;
-          if (ld_cg(pv) == sv) cnt = 0;
-          else *pv = sv;
-        }
         if (far_on && (Op::better(0u, 1u) ? sv > bound : sv < bound)) {
           // far: queue all of v's units again, once per round (stamp), and
           // skip this one now
@@ -260,6 +254,13 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
             dv = v;
             ddeg = r1 - r0;
           }
+        }
+        if (a.procv && cnt) {
+          // chunk ids v + rp[v]/C + ch are distinct across vertices; a
+          // deferred chunk is not relaxed now, so it records nothing
+          uint32_t* pv = a.procv + v + (r0 >> a.cshift) + ch;
+          if (ld_cg(pv) == sv) cnt = 0;
+          else *pv = sv;
         }
       }
       if (far_on) {

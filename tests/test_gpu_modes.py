@@ -60,3 +60,61 @@ def test_ablation_modes_exact(env, knobs):
     finally:
         ctx.set_tuning("slab_max", 128)
         ctx.set_tuning("prune", 1)
+
+
+@pytest.fixture(scope="module")
+def env2():
+    """Two mask words, a skewed degree mix and a hub source, so that frontiers
+    grow past the pull threshold."""
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_10579_gb300 import svv
+    log = W.scaled_rmat(scale=14, edge_factor=16, n_snapshots=90, rate=0.002, seed=33, add_mode="skewed")
+    return svv, log, W.max_out_degree_vertex(log)
+
+
+_want = {}
+
+
+def _oracle(log, t, src, b, L):
+    key = (id(log), t, src, b, L)
+    if key not in _want:
+        _want[key] = oracle.query(log, t, src, b, L)
+    return _want[key]
+
+
+@pytest.mark.parametrize("knobs", [
+    {"pull_pct": 0},                                   # push rounds only
+    {"pull_pct": 1},                                   # pull almost every round
+    {"skip_same": 0},
+    {"delta_sssp": 40, "delta_sswp": 40},              # near-far deferral
+    {"relax_lanes": 8}, {"relax_lanes": 16},
+    {"graph": 1},
+])
+def test_solver_knobs_exact(env2, knobs):
+    """Every launch knob changes only the work, never the values."""
+    svv, log, src = env2
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        for k, v in knobs.items():
+            ctx.set_tuning(k, v)
+        for t in (0, 1, 2, 3):
+            for b, L in [(0, 90), (10, 70)]:
+                np.testing.assert_array_equal(svv.to_u32(ctx.query(t, src, b, L)), _oracle(log, t, src, b, L))
+
+
+@pytest.mark.parametrize("knobs", [
+    {"solve_chunk": 16, "relax_chunk": 8, "qrs_chunk": 64},
+    {"solve_chunk": 256, "relax_chunk": 128, "qrs_chunk": 1024},
+    {"pull": 0},                                       # no transposed graph
+])
+def test_load_time_knobs_exact(env2, knobs):
+    """Knobs fixed when the graph is loaded (chunk sizes, the transposed
+    graph) change only the work."""
+    svv, log, src = env2
+    with svv.Context(0) as ctx:
+        for k, v in knobs.items():
+            ctx.set_tuning(k, v)
+        ctx.load_log(log)
+        for t in (0, 1, 2, 3):
+            np.testing.assert_array_equal(svv.to_u32(ctx.query(t, src, 5, 80)), _oracle(log, t, src, 5, 80))
