@@ -188,7 +188,11 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
           const uint32_t idx = (ch << 7) + 32u * j + lane;
           if (idx < ntot && lane == (unsigned)(__ffs(grp) - 1) && Op::better(best, ld_val(a.val + d[j]))) {
             Op::red(a.val + d[j], best);
-            if (atomicExch(a.stamp + d[j], stamp_next) != stamp_next) ++changed;
+            // a plain store: the next round finds the changed vertices from
+            // the stamps, so `changed` only needs to be zero exactly when
+            // nothing changed (it may count a vertex more than once)
+            a.stamp[d[j]] = stamp_next;
+            ++changed;
           }
         }
       }
