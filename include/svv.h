@@ -286,7 +286,9 @@ svv_status svv_solve_snapshot_noalloc(svv_type type, uint32_t V, uint64_t E, uin
  * initialisation; out[r] for r >= 1 = (frontier units << 40) | start time of
  * round r (ns, low 40 bits); entries past the last round are 0.  `out` is a
  * HOST array of `cap` entries (at most 4096 are written); *n_out receives the
- * number written. */
+ * number written.  Phase 3 = subgraph extraction: out[0..4] = device time (ns,
+ * %globaltimer) at which its five passes began (counts, rows, kept-edge
+ * counts, scan, fill), out[5] = when the last CTA finished. */
 svv_status svv_get_round_trace(svv_ctx *ctx, uint32_t phase, uint64_t *out, uint32_t cap,
                                uint32_t *n_out);
 

@@ -287,7 +287,7 @@ svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
     if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "round_trace is 0 or 1");
     if (v && !c->trace) {
       DeviceGuard dg(c->device);
-      if (cudaMalloc(&c->trace, 3 * kTraceCap * sizeof(unsigned long long)) != cudaSuccess) {
+      if (cudaMalloc(&c->trace, 4 * kTraceCap * sizeof(unsigned long long)) != cudaSuccess) {
         c->trace = nullptr;
         return cuda_fail(c, cudaGetLastError(), "trace buffer");
       }
@@ -574,7 +574,7 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
   a1.ctl = c->ctl + 0;
   a1.skip_nf = (wb == 0 && wl == c->g.S) ? 1 : 0;
   if (c->round_trace) {
-    cudaMemsetAsync(c->trace, 0, 3 * kTraceCap * sizeof(unsigned long long), s);
+    cudaMemsetAsync(c->trace, 0, 4 * kTraceCap * sizeof(unsigned long long), s);
     a1.trace = c->trace;
     a1.trace_cap = kTraceCap;
   }
@@ -619,6 +619,7 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
   q.ctl = c->ctl + 2;
   q.qerr = c->qerr;
   q.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
+  if (c->round_trace) q.trace = c->trace + 3 * kTraceCap;
   LaunchCfg qc = cfg_for(c, c->occ_qrs, kn.bps);
   if ((int64_t)qc.blocks > (int64_t)c->num_sms * 4) qc.blocks = c->num_sms * 4;
   if ((e = launch_qrs(q, qc, s)) != cudaSuccess) return cuda_fail(c, e, "launch subgraph extraction");
@@ -990,7 +991,7 @@ svv_status svv_get_bounds(svv_ctx* c, uint32_t* cap, uint32_t* cup, uint32_t* ro
 }
 
 svv_status svv_get_round_trace(svv_ctx* c, uint32_t phase, uint64_t* out, uint32_t cap, uint32_t* n_out) {
-  if (!c || !out || !n_out || phase > 2) return SVV_EINVAL;
+  if (!c || !out || !n_out || phase > 3) return SVV_EINVAL;
   *n_out = 0;
   if (!c->trace) return fail(c, SVV_EINVAL, "round_trace was never enabled");
   DeviceGuard dg(c->device);

@@ -125,6 +125,7 @@ struct QrsArgs {
   TeamCtl* ctl;           // aux[0]=U, aux[1]=#units, aux[2]=E_Q, aux[3]=#masked
   uint32_t* qerr;
   unsigned long long spin_ns;
+  unsigned long long* trace;  // optional: start ns of each of the five passes, then the end
 };
 
 struct RelaxArgs {

@@ -98,65 +98,81 @@ __device__ void qrs_walk(const QrsArgs& a, const Team& t, uint32_t NU, unsigned*
     }
     const uint32_t incl = warp_incl_scan(cnt, lane);
     const uint32_t total = __shfl_sync(kFullMask, incl, 31);
-    for (uint32_t p0 = 0; p0 < total; p0 += 32u) {
-      const uint32_t p = p0 + lane;
-      const int k = warp_owner(incl, p < total ? p : total - 1u);
-      const uint32_t ik = __shfl_sync(kFullMask, incl, k);
-      const uint32_t ck = __shfl_sync(kFullMask, cnt, k);
-      const uint32_t bk = __shfl_sync(kFullMask, beg, k);
-      const uint32_t fk = __shfl_sync(kFullMask, fe, k);
-      const uint32_t nk = __shfl_sync(kFullMask, nfb, k);
-      const uint32_t rk = __shfl_sync(kFullMask, r, k);
-      bool isF = false, isM = false;
-      uint32_t rx = kNone, w = 0;
-      const uint64_t* m = nullptr;
-      if (p < total) {
-        const uint32_t e = bk + (p - (ik - ck));
-        const uint2 ew = __ldg(g.cw + e);
-        rx = a.row[ew.x];
-        w = ew.y;
-        if (rx != kNone) {
-          if (e < fk) {
-            isF = true;
-          } else {
-            m = g.nfmask + (size_t)(nk + (e - fk)) * g.W;
-            bool any, all;
-            window_any_all(m, a.win, any, all);
-            isF = all;
-            isM = any && !all;
+    // two 32-edge steps per iteration: both steps' loads are issued before
+    // either step's counts or writes
+    for (uint32_t p0 = 0; p0 < total; p0 += 64u) {
+      int kk[2];
+      uint32_t rkk[2], rx[2], w[2];
+      bool isF[2], isM[2];
+      const uint64_t* m[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t p = p0 + 32u * h + lane;
+        const int k = warp_owner(incl, p < total ? p : total - 1u);
+        const uint32_t ik = __shfl_sync(kFullMask, incl, k);
+        const uint32_t ck = __shfl_sync(kFullMask, cnt, k);
+        const uint32_t bk = __shfl_sync(kFullMask, beg, k);
+        const uint32_t fk = __shfl_sync(kFullMask, fe, k);
+        const uint32_t nk = __shfl_sync(kFullMask, nfb, k);
+        kk[h] = k;
+        rkk[h] = __shfl_sync(kFullMask, r, k);
+        isF[h] = isM[h] = false;
+        rx[h] = kNone;
+        w[h] = 0;
+        m[h] = nullptr;
+        if (p < total) {
+          const uint32_t e = bk + (p - (ik - ck));
+          const uint2 ew = __ldg(g.cw + e);
+          rx[h] = a.row[ew.x];
+          w[h] = ew.y;
+          if (rx[h] != kNone) {
+            if (e < fk) {
+              isF[h] = true;
+            } else {
+              m[h] = g.nfmask + (size_t)(nk + (e - fk)) * g.W;
+              bool any, all;
+              window_any_all(m[h], a.win, any, all);
+              isF[h] = all;
+              isM[h] = any && !all;
+            }
           }
         }
       }
-      const unsigned grp = __match_any_sync(kFullMask, p < total ? (uint32_t)k : 64u + lane);
-      const unsigned bF = __ballot_sync(kFullMask, isF), bM = __ballot_sync(kFullMask, isM);
-      const int leader = __ffs(grp) - 1;
-      const uint32_t nF = __popc(grp & bF), nM = __popc(grp & bM);
-      if (!FILL) {
-        if (lane == (unsigned)leader && p < total) {
-          if (nF) atomicAdd(a.qcnt + 2u * rk, nF);
-          if (nM) atomicAdd(a.qcnt + 2u * rk + 1u, nM);
-        }
-      } else {
-        uint32_t baseF = 0, baseM = 0;
-        if (lane == (unsigned)leader && p < total) {
-          if (nF) baseF = atomicAdd(a.cur + 2u * rk, nF);
-          if (nM) baseM = atomicAdd(a.cur + 2u * rk + 1u, nM);
-        }
-        baseF = __shfl_sync(kFullMask, baseF, leader);
-        baseM = __shfl_sync(kFullMask, baseM, leader);
-        if (isF) {
-          const uint32_t pos = baseF + __popc(grp & bF & lt);
-          a.qcw[pos] = make_uint2(rx, w);
-        } else if (isM) {
-          const uint32_t pos = baseM + __popc(grp & bM & lt);
-          a.qcw[pos] = make_uint2(rx, w);
-          const uint4 d = __ldcg(a.qrow + rk);
-          uint64_t* out = a.qmask + (size_t)(d.z + (pos - d.y)) * a.QW;
-          for (uint32_t j = 0; j < a.QW; ++j) {
-            uint64_t word = mask_extract(m, g.W, a.win.b + 64u * j);
-            const uint32_t left = a.win.l - 64u * j;
-            if (left < 64u) word &= (1ull << left) - 1ull;
-            out[j] = word;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t p = p0 + 32u * h + lane;
+        const uint32_t rk = rkk[h];
+        const unsigned grp = __match_any_sync(kFullMask, p < total ? (uint32_t)kk[h] : 64u + lane);
+        const unsigned bF = __ballot_sync(kFullMask, isF[h]), bM = __ballot_sync(kFullMask, isM[h]);
+        const int leader = __ffs(grp) - 1;
+        const uint32_t nF = __popc(grp & bF), nM = __popc(grp & bM);
+        if (!FILL) {
+          if (lane == (unsigned)leader && p < total) {
+            if (nF) atomicAdd(a.qcnt + 2u * rk, nF);
+            if (nM) atomicAdd(a.qcnt + 2u * rk + 1u, nM);
+          }
+        } else {
+          uint32_t baseF = 0, baseM = 0;
+          if (lane == (unsigned)leader && p < total) {
+            if (nF) baseF = atomicAdd(a.cur + 2u * rk, nF);
+            if (nM) baseM = atomicAdd(a.cur + 2u * rk + 1u, nM);
+          }
+          baseF = __shfl_sync(kFullMask, baseF, leader);
+          baseM = __shfl_sync(kFullMask, baseM, leader);
+          if (isF[h]) {
+            const uint32_t pos = baseF + __popc(grp & bF & lt);
+            a.qcw[pos] = make_uint2(rx[h], w[h]);
+          } else if (isM[h]) {
+            const uint32_t pos = baseM + __popc(grp & bM & lt);
+            a.qcw[pos] = make_uint2(rx[h], w[h]);
+            const uint4 d = __ldcg(a.qrow + rk);
+            uint64_t* out = a.qmask + (size_t)(d.z + (pos - d.y)) * a.QW;
+            for (uint32_t j = 0; j < a.QW; ++j) {
+              uint64_t word = mask_extract(m[h], g.W, a.win.b + 64u * j);
+              const uint32_t left = a.win.l - 64u * j;
+              if (left < 64u) word &= (1ull << left) - 1ull;
+              out[j] = word;
+            }
           }
         }
       }
@@ -173,6 +189,7 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
   const uint32_t C = 1u << a.cshift;
 
   // ---- P1: unstable vertices and their units, per CTA vertex range
+  if (a.trace && b == 0 && tid == 0) a.trace[0] = global_ns();
   const unsigned long long per = (((unsigned long long)V + nb - 1) / nb + 31ull) & ~31ull;
   const uint32_t lo = (uint32_t)min((unsigned long long)V, per * b);
   const uint32_t hi = (uint32_t)min((unsigned long long)V, per * b + per);
@@ -193,6 +210,7 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
   if (!t.sync()) return false;
 
   // ---- P2: rows and units in vertex order
+  if (a.trace && b == 0 && tid == 0) a.trace[1] = global_ns();
   uint32_t U = 0, NU = 0;
   {
     uint32_t o_r = 0, o_u = 0, t_r = 0, t_u = 0;
@@ -225,16 +243,27 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
       }
       uint32_t ef, eu, tf, tu;
       block_excl_scan2(flag, nu, ef, eu, tf, tu);
+      const uint32_t r = o_r + ef;
       if (v < hi) {
-        const uint32_t r = o_r + ef;
         a.row[v] = flag ? r : kNone;
         if (flag) {
           a.uv[r] = v;
           a.qcnt[2 * r] = 0u;
           a.qcnt[2 * r + 1] = 0u;
-          for (uint32_t j = 0; j < nu; ++j)
-            a.units[o_u + eu + j] = (unsigned long long)r | ((unsigned long long)j << 32);
         }
+      }
+      // the warp writes its vertices' units together, so a hub's hundreds
+      // of units do not serialise on one thread
+      const unsigned lane = tid & 31u;
+      const uint32_t incl = warp_incl_scan(nu, lane);
+      const uint32_t wtot = __shfl_sync(kFullMask, incl, 31);
+      for (uint32_t j0 = 0; j0 < wtot; j0 += 32u) {
+        const uint32_t j = j0 + lane;
+        const int k = warp_owner(incl, j < wtot ? j : wtot - 1u);
+        const uint32_t ik = __shfl_sync(kFullMask, incl, k), nk = __shfl_sync(kFullMask, nu, k);
+        const uint32_t rk = __shfl_sync(kFullMask, r, k), ek = __shfl_sync(kFullMask, eu, k);
+        const uint32_t jj = j - (ik - nk);
+        if (j < wtot) a.units[o_u + ek + jj] = (unsigned long long)rk | ((unsigned long long)jj << 32);
       }
       o_r += tf;
       o_u += tu;
@@ -243,10 +272,12 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
   if (!t.sync()) return false;
 
   // ---- P3: per-row counts of kept edges
+  if (a.trace && b == 0 && tid == 0) a.trace[2] = global_ns();
   qrs_walk<false>(a, t, NU, &c->ticket[0]);
   if (!t.sync()) return false;
 
   // ---- P4: scan rows
+  if (a.trace && b == 0 && tid == 0) a.trace[3] = global_ns();
   const unsigned long long rper = (((unsigned long long)U + nb - 1) / nb + 31ull) & ~31ull;
   const uint32_t rlo = (uint32_t)min((unsigned long long)U, rper * b);
   const uint32_t rhi = (uint32_t)min((unsigned long long)U, rper * b + rper);
@@ -306,7 +337,9 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
   if (!t.sync()) return false;
 
   // ---- P5: fill
+  if (a.trace && b == 0 && tid == 0) a.trace[4] = global_ns();
   qrs_walk<true>(a, t, NU, &c->ticket[1]);
+  if (a.trace && tid == 0) atomicMax(a.trace + 5, global_ns());  // the last CTA to finish
   return true;
 }
 

@@ -331,10 +331,13 @@ def device_u32(address: int, n: int) -> np.ndarray:
 
 def svv_get_round_trace(ctx, phase: int):
     """[(frontier_units, start_ns)] per round of the last query's phase
-    (0 intersection, 1 union, 2 relaxation); round 0 holds (0, init_end_ns)."""
+    (0 intersection, 1 union, 2 relaxation); round 0 holds (0, init_end_ns).
+    Phase 3 (subgraph extraction): the six pass timestamps in ns."""
     buf = np.zeros(4096, np.uint64)
     n = ctypes.c_uint32()
     _check(ctx, lib().svv_get_round_trace(ctx, phase, _ptr(buf), 4096, ctypes.byref(n)))
+    if phase == 3:
+        return [int(x) for x in buf[:6]]
     out = []
     for i, x in enumerate(buf[:n.value].tolist()):
         if x == 0 and i > 0:
