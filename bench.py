@@ -17,7 +17,7 @@ bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
-import gc
+import gc as pygc
 import json
 import os
 import statistics
@@ -617,7 +617,7 @@ def main():
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     phase_ms = {k: 0.0 for k in ("cap", "cup", "qrs", "relax", "scatter")}
     all_stats = []
-    gc.disable()  # each query returns to the host: keep collector pauses out of the timed steps
+    pygc.disable()  # each query returns to the host: keep collector pauses out of the timed steps
     for i in range(args.steps):
         starts[i].record(stream)
         sts = step()
@@ -628,7 +628,7 @@ def main():
                 phase_ms[k] += st["ms_" + k]
         all_stats.append(sts)
     torch.cuda.synchronize()
-    gc.enable()
+    pygc.enable()
     barrier(world)
     clocks = sampler.stop() if sampler else None
     ms_total = sum(s.elapsed_time(e) for s, e in zip(starts, ends))

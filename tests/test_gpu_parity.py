@@ -118,6 +118,22 @@ def test_random_logs(svv, seed):
                     np.testing.assert_array_equal(_plain(svv, ctx, t, src, b, L), want)
 
 
+def test_saturating_weights(svv):
+    """Weights near 2^32: SSSP sums saturate at 0xFFFFFFFE (never reaching the
+    unreachable code), SSWP/SSNP bottlenecks take the huge weights as they are."""
+    log = W.random_small_log(17, V=150, n_edges=900, S=70, n_add=12, n_del=12, w_lo=1 << 30,
+                             w_hi=(1 << 32) - 1)
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        for t in TYPES:
+            for src, b, L in [(0, 0, 70), (5, 3, 40), (9, 60, 10)]:
+                want = oracle.query(log, t, src, b, L)
+                if t == 0:
+                    assert (want == 0xFFFFFFFE).any()  # the case is exercised
+                np.testing.assert_array_equal(_iu(svv, ctx, t, src, b, L), want)
+                np.testing.assert_array_equal(_plain(svv, ctx, t, src, b, L), want)
+
+
 @pytest.fixture(scope="module")
 def medium(svv):
     # scale-14 RMAT, 100 snapshots (two mask words), degree-skewed additions
