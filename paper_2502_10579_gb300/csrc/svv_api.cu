@@ -12,7 +12,7 @@ using namespace svv;
 
 namespace {
 
-void free_list(svv_ctx* c, std::vector<void*>& bufs) {
+void free_list(svv_ctx*, std::vector<void*>& bufs) {
   for (void* p : bufs) cudaFree(p);
   bufs.clear();
 }
