@@ -67,7 +67,8 @@ typedef enum {
 typedef struct {
     svv_type type;
     uint32_t source, win_begin, win_len;
-    uint32_t *out;          /* caller-owned DEVICE buffer of win_len*V uint32 */
+    uint32_t *out;          /* caller-owned buffer of win_len*V uint32: device memory,
+                               or host memory in svv_query_batch (staged copy) */
     svv_status status;      /* written by svv_query_batch */
 } svv_query_spec;
 
@@ -115,7 +116,10 @@ svv_status svv_build_versioned_csr(uint32_t V, uint32_t S, uint64_t n_inst, cons
  * live on the host, or on the device when inputs_on_device != 0; the library
  * copies them and the caller keeps ownership.  Internally each row is reordered
  * so that edges present in all S snapshots come first (Section 4.1), and edges
- * present in no snapshot are dropped.  Replaces any graph loaded before.
+ * present in no snapshot are dropped.  Unless the "pull" tuning key is 0, a
+ * transposed copy (in-edges sorted by target, 12 bytes per edge plus the masks
+ * of partial edges) is kept as well for the solves' pull rounds.  Replaces any
+ * graph loaded before.
  * SVV_EINVAL on a malformed CSR, S == 0, V >= 2^32-1 or E >= 2^32;
  * SVV_ENOMEM if the resident graph does not fit the budget. */
 svv_status svv_load(svv_ctx *ctx, uint32_t V, uint64_t E, uint32_t S, const uint64_t *row_ptr,
@@ -129,7 +133,8 @@ svv_status svv_load(svv_ctx *ctx, uint32_t V, uint64_t E, uint32_t S, const uint
  * DEVICE buffer of win_len*V uint32 (e.g. a torch tensor).  Work is ordered on
  * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream); the call
  * returns after the stream reaches the end of the query, with its status.
- * `out` is written only when the result is SVV_OK.
+ * On failure `out` holds no valid result (a window of more than 128 snapshots
+ * is relaxed and written slab by slab, so earlier slabs may have been written).
  * SVV_EINVAL on type, source >= V, win_len == 0 or win_begin+win_len > S. */
 svv_status svv_query(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
                      uint32_t win_len, uint32_t *out, void *cuda_stream);
