@@ -23,11 +23,20 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
   const uint32_t lps = __ffs(LP) - 1;  // LP is a power of two
   const uint32_t snap0 = a.win.b + a.s0;  // absolute snapshot of slab column 0
 
-  // ---- round 0a: values and stamps
-  const unsigned long long nval = (unsigned long long)U << lps;
-  for (unsigned long long idx = gtid; idx < nval; idx += nthreads)
-    a.val[idx] = a.rI[a.uv[(uint32_t)(idx >> lps)]];
-  for (uint32_t r = gtid; r < U; r += nthreads) a.stamp[r] = 0u;
+  // ---- round 0a: values and stamps.  A warp reads the starting values of
+  // 32 rows at once (a lane per row), then writes those rows together (a
+  // lane per column), so the dependent loads are paid once per 32 rows.
+  for (uint32_t r0 = gwarp * 32u; r0 < U; r0 += nwarps * 32u) {
+    const uint32_t r = r0 + lane;
+    const uint32_t x = r < U ? a.rI[a.uv[r]] : 0u;
+    if (r < U) a.stamp[r] = 0u;
+    const uint32_t nr = min(32u, U - r0);
+    for (uint32_t k = 0; k < nr; ++k) {
+      const uint32_t xv = __shfl_sync(kFullMask, x, k);
+      uint32_t* row = a.val + ((size_t)(r0 + k) << lps);
+      for (uint32_t i = lane; i < LP; i += 32u) row[i] = xv;
+    }
+  }
   if (!t.sync()) return false;
   if (a.trace && gtid == 0 && a.trace_cap) a.trace[0] = global_ns() & 0xFFFFFFFFFFull;
 
@@ -94,20 +103,29 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
           }
         }
       }
+      // lane h claims edge h's target (the HS stamp exchanges run side by
+      // side) and one warp append queues every claimed row
+      unsigned anyb = 0;
 #pragma unroll
-      for (int h = 0; h < HS; ++h) {
-        const bool any_imp = __any_sync(kFullMask, imp[h]);
-        bool push = false;
-        uint32_t deg = 0;
-        if (any_imp && lane == 0) {
-          const uint4 d = a.qrow[ex[h]];
-          if (atomicExch(a.stamp + ex[h], 1u) != 1u) {
-            push = true;
-            deg = d.w - d.x;
-          }
+      for (int h = 0; h < HS; ++h) anyb |= (__any_sync(kFullMask, imp[h]) ? 1u : 0u) << h;
+      uint32_t px = 0;
+      bool claim = false;
+#pragma unroll
+      for (int h = 0; h < HS; ++h)
+        if (lane == (unsigned)h) {
+          px = ex[h];
+          claim = (anyb >> h) & 1u;
         }
-        stage_push_units(push, ex[h], deg, a.cshift, st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
+      bool push = false;
+      uint32_t deg = 0;
+      if (claim) {
+        const uint4 d = a.qrow[px];
+        if (atomicExch(a.stamp + px, 1u) != 1u) {
+          push = true;
+          deg = d.w - d.x;
+        }
       }
+      stage_push_units(push, px, deg, a.cshift, st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
     }
   }
   stage_flush_cta(st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
