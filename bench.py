@@ -713,7 +713,7 @@ def main():
             "gpu_launches": args.steps * len(qs) * 5,
             "query_stats": [{k: v for k, v in st.items() if not k.startswith("ms_")} for st in last],
         }
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:  # timed on the host at N=1 only
             line["cpu_baseline"] = cpu_baseline(log, qs)
         print(json.dumps(line), flush=True)
     ctx.close()
