@@ -63,9 +63,14 @@ __global__ void __launch_bounds__(kNaThreads) noalloc_solve_kernel(NaArgs a) {
   const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t C = 1u << kNaChunkShift;
 
+  // starting values, and the CSR rules the queue bound rests on: row_ptr[0]
+  // = 0, rows never go backwards, row_ptr[V] = E (then every vertex's units
+  // fit the V + E/64 + 64 queue in every round)
   for (uint32_t v = gtid; v < a.V; v += nthreads) {
     a.val[v] = Op::kIdentity;
     a.stamp[v] = 0u;
+    const uint64_t r0 = __ldg(a.rp + v), r1 = __ldg(a.rp + v + 1);
+    if (r1 < r0 || r1 > a.E || (v == 0 && r0 != 0) || (v + 1 == a.V && r1 != a.E)) set_err(c, a.qerr, kErrInput);
   }
   if (!team_sync(c, a.qerr, gridDim.x, a.spin_ns)) return;
 
@@ -75,7 +80,8 @@ __global__ void __launch_bounds__(kNaThreads) noalloc_solve_kernel(NaArgs a) {
       a.val[a.source] = Op::kSource;
       a.stamp[a.source] = 1u;
       const uint64_t r0 = a.rp[a.source], r1 = a.rp[a.source + 1];
-      deg = (r1 >= r0 && r1 <= a.E) ? (uint32_t)(r1 - r0) : 0u;
+      if (r1 >= r0 && r1 <= a.E) deg = (uint32_t)(r1 - r0);
+      else set_err(c, a.qerr, kErrInput);
     }
     warp_push_units(lane == 0, a.source, deg, kNaChunkShift, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
   }
@@ -144,8 +150,12 @@ __global__ void __launch_bounds__(kNaThreads) noalloc_solve_kernel(NaArgs a) {
                 const uint32_t old = Op::atomic(a.val + x, cand);
                 if (Op::better(cand, old) && atomicExch(a.stamp + x, stamp_next) != stamp_next) {
                   const uint64_t x0 = __ldg(a.rp + x), x1 = __ldg(a.rp + x + 1);
-                  push = true;
-                  deg = (x1 >= x0 && x1 <= a.E) ? (uint32_t)(x1 - x0) : 0u;
+                  if (x1 >= x0 && x1 <= a.E) {
+                    push = true;
+                    deg = (uint32_t)(x1 - x0);
+                  } else {
+                    set_err(c, a.qerr, kErrInput);
+                  }
                 }
               }
             }
