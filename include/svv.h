@@ -145,9 +145,16 @@ svv_status svv_query(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_
  * instances from a device work queue and runs the whole intersection-union
  * pipeline of svv_query for each, with its own scratch, so instances overlap
  * on the GPU.  From 2M vertices, where one query's rounds already fill the
- * GPU, the instances run in order with svv_query's per-phase kernels, each
- * instance's status kept on the device and read back once at the end
- * ("batch_mode" tuning key: 0 = by graph size, 1 = one launch, 2 = in order).
+ * GPU, the instances run in QUERY GROUPS: up to "group_max" (default 8)
+ * instances of one type, in arrival order, share one intersection-graph solve
+ * and one union-graph solve -- one set of frontier rounds in which every
+ * vertex holds one value per member query (a query-oblivious frontier, as
+ * Section 4.2 shares one frontier between snapshots), so each round reads
+ * each edge once and ends at one barrier for the whole group -- and each
+ * member then runs its own stable compaction, subgraph extraction,
+ * relaxation and scatter.  Each instance's status is kept on the device and
+ * read back once at the end ("batch_mode" tuning key: 0 = by graph size,
+ * 1 = one launch, 2 = in order, in groups).
  * A spec's `out` may also be HOST memory (win_len*V uint32): the batch then
  * runs in order, and each such result is computed into one of two device
  * staging slots and copied back on a second stream while the next instance
@@ -250,7 +257,8 @@ svv_status svv_query_plain(svv_ctx *ctx, svv_type type, uint32_t source, uint32_
 svv_status svv_query_host(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
                           uint32_t win_len, uint32_t *out_host, void *cuda_stream);
 
-/* Step-level results of the last successful svv_query, for inspection: the
+/* Step-level results of the last successful svv_query (or of the last
+ * instance of an in-order svv_query_batch), for inspection: the
  * intersection-graph values (Section 3 Step 1, upper bound for SSSP/BFS, lower
  * for SSWP), the union-graph values, and the vertex -> relaxation-row map
  * (0xFFFFFFFF for a stable vertex, Theorem 2).  Each destination is a caller
@@ -268,12 +276,15 @@ svv_status svv_get_bounds(svv_ctx *ctx, uint32_t *cap, uint32_t *cup, uint32_t *
  * uint32 that receives the value of every vertex in snapshot `snapshot` (the
  * same values as row snapshot-win_begin of svv_query_plain).  No context is
  * needed: the call runs on the calling thread's current CUDA device, ordered
- * on `cuda_stream`, and returns once the result is in `out`.
+ * on `cuda_stream`, and synchronises that stream before it returns, so the
+ * result is in `out` when it returns.
  * Types SSSP, SSWP and BFS (SSNP gets SVV_EINVAL).
  * Working memory is a fixed 32 MiB device array inside the library, held by
  * every GPU that loads it until the process exits; a graph whose
  * 4*V + 16*(V + E/64 + 64) bytes (plus 1 KiB) exceed it is rejected with
- * SVV_EINVAL, as are bad arguments and a CSR the kernel finds malformed.  The
+ * SVV_EINVAL, as are bad arguments and a CSR the kernel finds malformed
+ * (row_ptr[0] != 0, a row that goes backwards, row_ptr[V] != E, a target >= V;
+ * the kernel checks each before it uses it).  The
  * first call on a device looks up that array's device address
  * (cudaGetSymbolAddress), so make it before any stream capture.  Every call
  * shares the array: calls that overlap on the GPU (other streams, other host
@@ -332,6 +343,14 @@ svv_status svv_autotune(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t w
  * instantiated graph in place for the next query of the same shape and
  * replays it; falls back to direct launches where capture is refused; phase
  * timing is not recorded in this mode),
+ * "group_max" (1..8, default 8: queries per group of an in-order batch and of
+ * the server from 2M vertices; 1 runs every query alone), "group_pull_pct" /
+ * "group_pull_pct_union" (0..100, defaults 15 / 100: a group's intersection /
+ * union solve pulls when its frontier holds more than this % of all work
+ * units; 0 or 100 = push only), "isolated_fast" (1 default: a query whose
+ * source has no out-edge in any snapshot is answered by one fill -- the
+ * source value at the source, unreachable everywhere else -- instead of the
+ * full pipeline; 0 runs the pipeline; results are identical),
  * "batch_teams" (teams of svv_query_batch and the server, 1..64; 0 = by graph
  * size: 8 up to 1M vertices, fewer above, 1 from 8M), "batch_mode" (0 = by
  * graph size, 1 = one launch, 2 = in order; see svv_query_batch), "relax_lanes" (8, 16, 32:

@@ -10,7 +10,7 @@
 
 using namespace svv;
 
-namespace {
+namespace svv {
 
 void free_list(svv_ctx*, std::vector<void*>& bufs) {
   for (void* p : bufs) cudaFree(p);
@@ -20,6 +20,7 @@ void free_list(svv_ctx*, std::vector<void*>& bufs) {
 void free_graph(svv_ctx* c) {
   free_serve(c);
   free_batch(c);
+  free_group(c);
   free_list(c, c->graph_bufs);
   free_list(c, c->scratch_bufs);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
@@ -136,7 +137,7 @@ svv_status finish(svv_ctx* c, cudaStream_t s, int nctl_copy) {
   return SVV_OK;
 }
 
-}  // namespace
+}  // namespace svv
 
 extern "C" {
 
@@ -185,7 +186,8 @@ svv_status svv_create(svv_ctx** out, int device, uint64_t budget) {
   c->occ_qrs = occupancy_qrs(c->threads);
   c->occ_relax = occupancy_relax(c->threads);
   c->occ_batch = occupancy_batch(c->threads);
-  if (c->occ_solve <= 0 || c->occ_qrs <= 0 || c->occ_relax <= 0 || c->occ_batch <= 0) {
+  c->occ_group = occupancy_group(c->threads);
+  if (c->occ_solve <= 0 || c->occ_qrs <= 0 || c->occ_relax <= 0 || c->occ_batch <= 0 || c->occ_group <= 0) {
     delete c;
     return SVV_ECUDA;
   }
@@ -280,6 +282,15 @@ svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
   } else if (k == "batch_mode") {
     if (v < 0 || v > 2) return fail(c, SVV_EINVAL, "batch_mode is 0 (by graph size), 1 (one launch) or 2 (in order)");
     c->batch_mode = (int)v;
+  } else if (k == "group_pull_pct" || k == "group_pull_pct_union") {
+    if (v < 0 || v > 100) return fail(c, SVV_EINVAL, k + " in [0, 100]");
+    c->group_pull_pct[k == "group_pull_pct" ? 0 : 1] = (uint32_t)v;
+  } else if (k == "isolated_fast") {
+    if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "isolated_fast is 0 or 1");
+    c->isolated_fast = v != 0;
+  } else if (k == "group_max") {
+    if (v < 1 || v > kGroupMax) return fail(c, SVV_EINVAL, "group_max in [1, 8]");
+    c->group_max = (uint32_t)v;
   } else if (k == "batch_teams") {
     if (v < 0 || v > 64) return fail(c, SVV_EINVAL, "batch_teams in [0, 64]");
     c->batch_teams = (int)v;
@@ -536,6 +547,10 @@ svv_status svv_load(svv_ctx* c, uint32_t V, uint64_t E, uint32_t S, const uint64
   c->pcap = (uint32_t)((uint64_t)V + (E2 >> 4) + 64);
   c->ecap = std::max<uint32_t>(E2, 1);
   c->g = g;
+  // out-degree over the edges present in some snapshot: a source without any
+  // reaches nothing in any window (the query's result is known without a solve)
+  c->hdeg.resize(V);
+  for (uint32_t v = 0; v < V; ++v) c->hdeg[v] = rp[v + 1] - rp[v];
   c->loaded = true;
   c->stats = svv_stats{};
   c->err.clear();
@@ -544,26 +559,59 @@ svv_status svv_load(svv_ctx* c, uint32_t V, uint64_t E, uint32_t S, const uint64
 
 }  // extern "C"
 
-namespace {
+namespace svv {
 
 // Enqueue every step of one query on stream s (no host synchronisation, so a
 // graph capture can record it).  With timing, CUDA events bracket the phases.
 // With rows_out set, the scatter is replaced by a copy of the relaxed rows
 // (compact output).
-struct CompactOut {
-  uint32_t* cap_out;
-  uint32_t* row_out;
-  uint32_t* rows_out;
-  uint64_t rows_cap;
-};
+
+bool source_is_isolated(const svv_ctx* c, uint32_t source) {
+  return source < c->hdeg.size() && c->hdeg[source] == 0 && c->isolated_fast;
+}
+
+// A source with no out-edge in any snapshot: both bounds (Section 3 Step 1)
+// hold the source value at the source and the identity everywhere else, every
+// vertex is stable (Theorem 2), and the result is that row in every window
+// snapshot.  One kernel writes the result, the bounds and the row map.
+svv_status enqueue_isolated(svv_ctx* c, int t, uint32_t source, uint32_t wl, uint32_t* out, cudaStream_t s,
+                            bool timing, const CompactOut* co) {
+  IsolatedArgs f{};
+  f.V = c->g.V;
+  f.L = co ? 0u : wl;
+  f.source = source;
+  f.ident = t == 1 ? 0u : kInf;
+  f.src_val = t == 1 ? kInf : 0u;
+  f.out = co ? nullptr : out;
+  f.rI = c->rI;
+  f.rU = c->rU;
+  f.row = c->row;
+  f.sms = (uint32_t)c->num_sms;
+  cudaError_t e = launch_isolated(f, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "launch isolated-source fill");
+  c->last_rI = c->rI;
+  c->last_rU = c->rU;
+  if (co) {
+    const size_t n = (size_t)c->g.V * sizeof(uint32_t);
+    if (co->cap_out && (e = cudaMemcpyAsync(co->cap_out, c->rI, n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return cuda_fail(c, e, "copy intersection values");
+    if (co->row_out && (e = cudaMemcpyAsync(co->row_out, c->row, n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return cuda_fail(c, e, "copy row map");
+  }
+  if (timing)
+    for (int i = 1; i <= 6; ++i) cudaEventRecord(c->ev[i], s);
+  return SVV_OK;
+}
 
 svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32_t wl, uint32_t* out,
                          cudaStream_t s, bool timing, float* ms_relax_out, float* ms_scatter_out,
-                         const CompactOut* co = nullptr) {
+                         const CompactOut* co) {
+  *ms_relax_out = *ms_scatter_out = 0.f;
   cudaError_t e = cudaMemsetAsync(c->ctl, 0, sizeof(TeamCtl) * 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->qerr, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "memset");
   if (timing) cudaEventRecord(c->ev[0], s);
+  if (source_is_isolated(c, source)) return enqueue_isolated(c, t, source, wl, out, s, timing, co);
 
   // a1: intersection graph (edges present in every window snapshot)
   const Knobs kn = knobs_of(c, t);
@@ -595,14 +643,30 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
   if (c->prune && (e = launch_solve(t, kPredAny, a2, cfg_for(c, c->occ_solve, kn.bps), s)) != cudaSuccess)
     return cuda_fail(c, e, "launch union solve");
   if (timing) cudaEventRecord(c->ev[2], s);
+  return enqueue_tail(c, t, wb, wl, out, c->rI, c->rU, s, timing, ms_relax_out, ms_scatter_out, co, false);
+}
+
+// a3-a6 of one query from its bound values rI (intersection graph) and rU
+// (union graph): stable compaction and subgraph extraction, then relaxation
+// and scatter per slab of at most 128 snapshots.  With `fresh` the phases'
+// control blocks are cleared first (a query whose bounds came from a group).
+svv_status enqueue_tail(svv_ctx* c, int t, uint32_t wb, uint32_t wl, uint32_t* out, const uint32_t* rI,
+                        const uint32_t* rU, cudaStream_t s, bool timing, float* ms_relax_out, float* ms_scatter_out,
+                        const CompactOut* co, bool fresh) {
+  cudaError_t e = cudaSuccess;
+  const Knobs kn = knobs_of(c, t);
+  if (fresh && (e = cudaMemsetAsync(c->ctl + 2, 0, sizeof(TeamCtl) * 2, s)) != cudaSuccess)
+    return cuda_fail(c, e, "memset");
+  c->last_rI = rI;
+  c->last_rU = rU;
   // a3+a4: stable compaction and the Q-relevant subgraph
   QrsArgs q{};
   q.g = c->g;
   q.win = Window{wb, wl};
   q.QW = ceil_div(wl, 64);
   q.prune = c->prune ? 1 : 0;
-  q.rI = c->rI;
-  q.rU = c->rU;
+  q.rI = rI;
+  q.rU = rU;
   q.row = c->row;
   q.uv = c->uv;
   q.part = c->part;
@@ -641,7 +705,7 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
     r.s0 = s0;
     r.ls = ls;
     r.QW = q.QW;
-    r.rI = c->rI;
+    r.rI = rI;
     r.row = c->row;
     r.uv = c->uv;
     r.qrow = c->qrow;
@@ -685,7 +749,7 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
     sa.V = c->g.V;
     sa.s0 = s0;
     sa.ls = ls;
-    sa.rI = c->rI;
+    sa.rI = rI;
     sa.row = c->row;
     sa.val = c->val;
     sa.LP = P * K;
@@ -706,7 +770,7 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
   }
   if (co) {
     const size_t n = (size_t)c->g.V * sizeof(uint32_t);
-    if (co->cap_out && (e = cudaMemcpyAsync(co->cap_out, c->rI, n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    if (co->cap_out && (e = cudaMemcpyAsync(co->cap_out, rI, n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       return cuda_fail(c, e, "copy intersection values");
     if (co->row_out && (e = cudaMemcpyAsync(co->row_out, c->row, n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       return cuda_fail(c, e, "copy row map");
@@ -764,7 +828,7 @@ svv_status graph_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32_t
   return SVV_OK;
 }
 
-}  // namespace
+}  // namespace svv
 
 namespace svv {
 
@@ -796,6 +860,28 @@ static svv_status ensure_bstage(svv_ctx* c, uint64_t words) {
   return SVV_OK;
 }
 
+// Groups of at most gmax instances of one type, each in arrival order, the
+// groups ordered by their first member.  An instance whose source has no
+// out-edge is answered by one fill and gets a group of its own.
+std::vector<std::vector<uint32_t>> form_groups(const svv_ctx* c, const BatchInstance* inst, uint32_t m,
+                                               uint32_t gmax) {
+  std::vector<std::vector<uint32_t>> groups;
+  int open[4] = {-1, -1, -1, -1};  // the group still filling, per type
+  for (uint32_t k = 0; k < m; ++k) {
+    if (source_is_isolated(c, inst[k].source)) {
+      groups.push_back({k});
+      continue;
+    }
+    const int t = std::max(0, std::min(3, inst[k].type));
+    if (open[t] < 0 || groups[open[t]].size() >= std::max<uint32_t>(1, gmax)) {
+      open[t] = (int)groups.size();
+      groups.emplace_back();
+    }
+    groups[open[t]].push_back(k);
+  }
+  return groups;
+}
+
 svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, const char* host_out,
                           uint32_t* qerr_dev, uint32_t* qerr_host, cudaStream_t s, float* ms) {
   uint32_t Lmax = 1, Lhost = 0;
@@ -810,34 +896,53 @@ svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, con
   for (auto& ev : c->bev)
     if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
   cudaEventRecord(c->bev[0], s);
-  // A host output is computed into a staging slot and copied back on the copy
-  // stream while the next instance computes; a slot is reused only after its
-  // last copy has finished.
+  // Instances run in groups of up to group_max of one type (in order of
+  // their first member): one pair of group solves gives every member its
+  // bounds, then each member runs its own phases.  A host output is computed
+  // into a staging slot and copied back on the copy stream while the next
+  // instance computes; a slot is reused only after its last copy has finished.
+  const std::vector<std::vector<uint32_t>> groups = form_groups(c, inst, m, c->group_max);
   bool used[2] = {false, false};
   uint32_t nh = 0;
-  for (uint32_t k = 0; k < m; ++k) {
-    float a = 0.f, b = 0.f;
-    uint32_t* out = inst[k].out;
-    int slot = -1;
-    if (host_out && host_out[k]) {
-      slot = (int)(nh++ & 1u);
-      if (used[slot] && (e = cudaStreamWaitEvent(s, c->ev_copied[slot], 0)) != cudaSuccess)
-        return cuda_fail(c, e, "staging wait");
-      out = c->bstage[slot];
+  for (const auto& grp : groups) {
+    const bool grouped = grp.size() > 1;
+    if (grouped) {
+      BatchInstance gi[kGroupMax];
+      for (size_t j = 0; j < grp.size(); ++j) gi[j] = inst[grp[j]];
+      if ((st = enqueue_group_bounds(c, gi[0].type, gi, (uint32_t)grp.size(), s))) return st;
     }
-    if ((st = enqueue_query(c, inst[k].type, inst[k].source, inst[k].wb, inst[k].wl, out, s, false, &a, &b)))
-      return st;
-    if ((e = cudaMemcpyAsync(qerr_dev + k, c->qerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-      return cuda_fail(c, e, "batch status copy");
-    if (slot >= 0) {
-      const size_t bytes = (size_t)inst[k].wl * c->g.V * sizeof(uint32_t);
-      e = cudaEventRecord(c->ev_done[slot], s);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->ev_done[slot], 0);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(inst[k].out, out, bytes, cudaMemcpyDeviceToHost, c->copy_stream);
-      if (e == cudaSuccess) e = cudaEventRecord(c->ev_copied[slot], c->copy_stream);
-      if (e != cudaSuccess) return cuda_fail(c, e, "copying a result to the host");
-      used[slot] = true;
+    for (size_t j = 0; j < grp.size(); ++j) {
+      const uint32_t k = grp[j];
+      float a = 0.f, b = 0.f;
+      uint32_t* out = inst[k].out;
+      int slot = -1;
+      if (host_out && host_out[k]) {
+        slot = (int)(nh++ & 1u);
+        if (used[slot] && (e = cudaStreamWaitEvent(s, c->ev_copied[slot], 0)) != cudaSuccess)
+          return cuda_fail(c, e, "staging wait");
+        out = c->bstage[slot];
+      }
+      if (grouped) {
+        if ((e = cudaMemcpyAsync(c->qerr, c->gerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+          return cuda_fail(c, e, "group status copy");
+        if ((st = enqueue_tail(c, inst[k].type, inst[k].wb, inst[k].wl, out, c->gI[j], c->gU[j], s, false, &a, &b,
+                               nullptr, true)))
+          return st;
+      } else if ((st = enqueue_query(c, inst[k].type, inst[k].source, inst[k].wb, inst[k].wl, out, s, false, &a, &b))) {
+        return st;
+      }
+      if ((e = cudaMemcpyAsync(qerr_dev + k, c->qerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(c, e, "batch status copy");
+      if (slot >= 0) {
+        const size_t bytes = (size_t)inst[k].wl * c->g.V * sizeof(uint32_t);
+        e = cudaEventRecord(c->ev_done[slot], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->ev_done[slot], 0);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(inst[k].out, out, bytes, cudaMemcpyDeviceToHost, c->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_copied[slot], c->copy_stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copying a result to the host");
+        used[slot] = true;
+      }
     }
   }
   cudaEventRecord(c->bev[1], s);
@@ -982,8 +1087,10 @@ svv_status svv_get_bounds(svv_ctx* c, uint32_t* cap, uint32_t* cup, uint32_t* ro
   ServeFence fence(c, s);
   const size_t n = (size_t)c->g.V * sizeof(uint32_t);
   cudaError_t e = cudaSuccess;
-  if (cap) e = cudaMemcpyAsync(cap, c->rI, n, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && cup) e = cudaMemcpyAsync(cup, c->rU, n, cudaMemcpyDeviceToDevice, s);
+  const uint32_t* rI = c->last_rI ? c->last_rI : c->rI;
+  const uint32_t* rU = c->last_rU ? c->last_rU : c->rU;
+  if (cap) e = cudaMemcpyAsync(cap, rI, n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && cup) e = cudaMemcpyAsync(cup, rU, n, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess && row) e = cudaMemcpyAsync(row, c->row, n, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "copying bounds");

@@ -214,6 +214,11 @@ extern "C" svv_status svv_query_batch(svv_ctx* c, uint32_t n, svv_query_spec* sp
   const uint32_t m = (uint32_t)inst.size();
   cudaStream_t s = (cudaStream_t)stream;
   svv_status st;
+  // a failure of the whole call leaves no valid result: every spec says so
+  auto fail_all = [&](svv_status why) {
+    for (uint32_t k = 0; k < m; ++k) specs[idx[k]].status = why;
+    return why;
+  };
   // outputs in host memory (page-locked or not) run in order, staged
   std::vector<char> host_out(m, 0);
   bool any_host = false;
@@ -227,14 +232,14 @@ extern "C" svv_status svv_query_batch(svv_ctx* c, uint32_t n, svv_query_spec* sp
     any_host |= host_out[k] != 0;
   }
   if (any_host || !batch_one_launch(c)) {
-    if ((st = ensure_instances(c, m))) return st;
+    if ((st = ensure_instances(c, m))) return fail_all(st);
     std::vector<uint32_t> qerr(m);
     float ms = 0.f;
     {
       ServeFence fence(c, s);
       if ((st = batch_in_order(c, inst.data(), m, any_host ? host_out.data() : nullptr, c->batch.d_qerr,
                                qerr.data(), s, &ms)))
-        return st;
+        return fail_all(st);
     }
     svv_status overall = first_bad;
     for (uint32_t k = 0; k < m; ++k) {
@@ -249,22 +254,22 @@ extern "C" svv_status svv_query_batch(svv_ctx* c, uint32_t n, svv_query_spec* sp
     c->err.clear();
     return SVV_OK;
   }
-  if ((st = ensure_pool(c, default_teams(c), Lmax))) return st;
-  if ((st = ensure_instances(c, m))) return st;
+  if ((st = ensure_pool(c, default_teams(c), Lmax))) return fail_all(st);
+  if ((st = ensure_instances(c, m))) return fail_all(st);
   BatchPool& p = c->batch;
   cudaError_t e = cudaMemcpyAsync(p.d_inst, inst.data(), sizeof(BatchInstance) * m, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.d_ctl, 0, sizeof(TeamCtl) * kBatchCtl * p.teams, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.d_next, 0, sizeof(unsigned), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.d_qerr, 0, sizeof(uint32_t) * m, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.d_done, 0, sizeof(uint32_t) * m, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "batch setup");
+  if (e != cudaSuccess) return fail_all(cuda_fail(c, e, "batch setup"));
   BatchArgs b = batch_args(c);
   b.n_inst = m;
   // fewer instances than teams: fewer, larger teams over the same grid
   const int teams = std::min<int>(p.teams, (int)m);
   b.team_blocks = (uint32_t)(p.teams * (int)p.team_blocks / teams);
   if ((e = launch_batch(b, LaunchCfg{teams * (int)b.team_blocks, 512}, s)) != cudaSuccess)
-    return cuda_fail(c, e, "launch batch");
+    return fail_all(cuda_fail(c, e, "launch batch"));
   std::vector<uint32_t> qerr(m), done(m);
   std::vector<unsigned long long> t0(m), t1(m);
   e = cudaMemcpyAsync(qerr.data(), p.d_qerr, 4ull * m, cudaMemcpyDeviceToHost, s);
@@ -272,7 +277,7 @@ extern "C" svv_status svv_query_batch(svv_ctx* c, uint32_t n, svv_query_spec* sp
   if (e == cudaSuccess) e = cudaMemcpyAsync(t0.data(), p.d_t0, 8ull * m, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(t1.data(), p.d_t1, 8ull * m, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "batch");
+  if (e != cudaSuccess) return fail_all(cuda_fail(c, e, "batch"));
   svv_status overall = first_bad;
   unsigned long long lo = ~0ull, hi = 0;
   for (uint32_t k = 0; k < m; ++k) {

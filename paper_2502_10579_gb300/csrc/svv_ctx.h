@@ -180,6 +180,25 @@ struct svv_ctx {
   int occ_batch = 0;
   cudaEvent_t bev[2] = {};  // span of an in-order batch
 
+  // query groups: lane rows of the two bounds, per-lane planar copies, lane
+  // words of the partial edges, the group's error word
+  uint32_t group_max = svv::kGroupMax;  // queries per group (1 = every query alone)
+  // pull threshold of the group solves (intersection, union), % of all units:
+  // a group pull round gathers a whole lane row per in-edge, so groups pull later
+  uint32_t group_pull_pct[2] = {15, 100};
+  int occ_group = 0;
+  bool group_ready = false;
+  std::vector<void*> group_bufs;
+  uint32_t *gcap = nullptr, *gcup = nullptr, *gnfl = nullptr, *gipl = nullptr, *gerr = nullptr;
+  uint32_t* gI[svv::kGroupMax] = {};
+  uint32_t* gU[svv::kGroupMax] = {};
+  // host copy of each vertex's out-degree over edges present in some snapshot
+  std::vector<uint32_t> hdeg;
+  bool isolated_fast = true;  // answer queries from a source without out-edges by one fill
+  // bounds the last query's phases read (svv_get_bounds)
+  const uint32_t* last_rI = nullptr;
+  const uint32_t* last_rU = nullptr;
+
   svv_stats stats{};
 };
 
@@ -252,6 +271,32 @@ inline void slab_shape(uint32_t ls, uint32_t& P, uint32_t& K) {
     K = 4;
   }
 }
+
+// host helpers of the query pipeline (svv_api.cu)
+struct CompactOut {
+  uint32_t* cap_out;
+  uint32_t* row_out;
+  uint32_t* rows_out;
+  uint64_t rows_cap;
+};
+Knobs knobs_of(const svv_ctx* c, int type);
+LaunchCfg cfg_for(const svv_ctx* c, int occ, int bps);
+SolveArgs solve_base(svv_ctx* c, uint32_t wb, uint32_t wl, int type, const Knobs& kn);
+svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32_t wl, uint32_t* out,
+                         cudaStream_t s, bool timing, float* ms_relax_out, float* ms_scatter_out,
+                         const CompactOut* co = nullptr);
+bool source_is_isolated(const svv_ctx* c, uint32_t source);
+svv_status enqueue_isolated(svv_ctx* c, int t, uint32_t source, uint32_t wl, uint32_t* out, cudaStream_t s,
+                            bool timing, const CompactOut* co);
+svv_status enqueue_tail(svv_ctx* c, int t, uint32_t wb, uint32_t wl, uint32_t* out, const uint32_t* rI,
+                        const uint32_t* rU, cudaStream_t s, bool timing, float* ms_relax_out, float* ms_scatter_out,
+                        const CompactOut* co, bool fresh);
+
+// query groups (svv_group_api.cu): the bounds of up to group_max same-type
+// queries from one pair of group solves, then each query's own phases
+svv_status ensure_group(svv_ctx* c);
+svv_status enqueue_group_bounds(svv_ctx* c, int type, const BatchInstance* inst, uint32_t n, cudaStream_t s);
+void free_group(svv_ctx* c);
 
 void free_batch(svv_ctx* c);
 void free_serve(svv_ctx* c);

@@ -1,0 +1,128 @@
+// svv_group_api.cu -- host side of query groups: their scratch, and the two
+// group solves (svv_group.cuh) that give every member query its
+// intersection- and union-graph values (Section 3 Step 1) from one set of
+// frontier rounds.  Each member then runs its own stable compaction, subgraph
+// extraction, relaxation and scatter (enqueue_tail) from its lane's planar
+// copy of the bounds.
+#include "svv_ctx.h"
+
+namespace svv {
+
+void free_group(svv_ctx* c) {
+  c->last_rI = c->last_rU = nullptr;
+  for (void* p : c->group_bufs) cudaFree(p);
+  c->group_bufs.clear();
+  c->gcap = c->gcup = c->gnfl = c->gipl = c->gerr = nullptr;
+  for (int k = 0; k < kGroupMax; ++k) c->gI[k] = c->gU[k] = nullptr;
+  c->group_ready = false;
+}
+
+svv_status ensure_group(svv_ctx* c) {
+  if (c->group_ready) return SVV_OK;
+  const uint64_t V = c->g.V, NF = std::max<uint32_t>(c->g.NF, 1);
+  svv_status st;
+  if ((st = alloc_n(c, c->group_bufs, V * kGroupMax, &c->gcap)) ||
+      (st = alloc_n(c, c->group_bufs, V * kGroupMax, &c->gcup)) || (st = alloc_n(c, c->group_bufs, NF, &c->gnfl)) ||
+      (st = alloc_n(c, c->group_bufs, NF, &c->gipl)) || (st = alloc_n(c, c->group_bufs, 1, &c->gerr))) {
+    free_group(c);
+    return st;
+  }
+  for (int k = 0; k < kGroupMax; ++k) {
+    if ((st = alloc_n(c, c->group_bufs, V, &c->gI[k])) || (st = alloc_n(c, c->group_bufs, V, &c->gU[k]))) {
+      free_group(c);
+      return st;
+    }
+  }
+  c->group_ready = true;
+  return SVV_OK;
+}
+
+// The two bound solves of n (2..kGroupMax) same-type queries, lane k = inst[k],
+// then the split into gI[k] (intersection values) and gU[k] (union values).
+// The group's error word ends up in gerr: each member's phases start from it.
+svv_status enqueue_group_bounds(svv_ctx* c, int t, const BatchInstance* inst, uint32_t n, cudaStream_t s) {
+  if (n < 1 || n > (uint32_t)kGroupMax) return fail(c, SVV_EINTERNAL, "group size out of range");
+  svv_status st = ensure_group(c);
+  if (st) return st;
+  const uint32_t KL = n <= 4 ? 4u : 8u;
+  const Knobs kn = knobs_of(c, t);
+  cudaError_t e = cudaMemsetAsync(c->ctl + 4, 0, sizeof(TeamCtl) * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->qerr, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+
+  LanesArgs la{};
+  la.g = c->g;
+  la.nlanes = n;
+  for (uint32_t k = 0; k < n; ++k) la.win[k] = Window{inst[k].wb, inst[k].wl};
+  la.nflanes = c->gnfl;
+  la.iplanes = c->g.ifd ? c->gipl : nullptr;
+  if ((e = launch_group_lanes(la, s)) != cudaSuccess) return cuda_fail(c, e, "launch lane words");
+
+  const SolveArgs base = solve_base(c, 0, 1, t, kn);
+  GroupArgs a{};
+  a.g = c->g;
+  a.nlanes = n;
+  for (uint32_t k = 0; k < n; ++k) a.source[k] = inst[k].source;
+  a.init = kInitSource;
+  a.val = c->gcap;
+  a.nflanes = c->gnfl;
+  a.iplanes = c->gipl;
+  a.stamp = c->stamp;
+  a.q0 = c->q0;
+  a.q1 = c->q1;
+  a.qcap = c->qcap;
+  a.cshift = kn.solve_cs;
+  a.ctl = c->ctl + 4;
+  a.qerr = c->qerr;
+  a.maxit = c->maxit ? c->maxit : c->g.V + 2u;
+  a.spin_ns = base.spin_ns;
+  // pull thresholds of the group solves (0 = push only)
+  uint32_t pull_u[2] = {0, 0}, push_v[2] = {0, 0};
+  for (int i = 0; i < 2; ++i) {
+    const uint32_t pct = c->group_pull_pct[i];
+    if (c->g.ifd && pct && pct < 100) {
+      const uint64_t all_units = (uint64_t)c->g.V + (c->g.E >> kn.solve_cs);
+      pull_u[i] = (uint32_t)std::max<uint64_t>(1, all_units * pct / 100);
+      push_v[i] = (uint32_t)std::max<uint64_t>(1, (uint64_t)c->g.V * pct / 100);
+    }
+  }
+  a.pull_units = pull_u[0];
+  a.push_verts = push_v[0];
+  if (c->round_trace) {  // phases 0 and 1 of the round trace: the group's two solves
+    cudaMemsetAsync(c->trace, 0, 2 * kTraceCap * sizeof(unsigned long long), s);
+    a.trace = c->trace;
+    a.trace_cap = kTraceCap;
+  }
+  const LaunchCfg cfg = cfg_for(c, c->occ_group, kn.bps);
+  if ((e = launch_group_solve(t, KL, kPredAll, a, cfg, s)) != cudaSuccess)
+    return cuda_fail(c, e, "launch group intersection solve");
+  SplitArgs sp{};
+  sp.V = c->g.V;
+  sp.nlanes = n;
+  sp.KL = KL;
+  sp.cap = c->gcap;
+  sp.cup = c->gcap;
+  if (c->prune) {  // without pruning the union values are never read
+    GroupArgs b = a;
+    b.init = kInitSeed;
+    b.base = c->gcap;
+    b.val = c->gcup;
+    b.ctl = c->ctl + 5;
+    b.pull_units = pull_u[1];
+    b.push_verts = push_v[1];
+    if (c->round_trace) b.trace = c->trace + kTraceCap;
+    if ((e = launch_group_solve(t, KL, kPredAny, b, cfg, s)) != cudaSuccess)
+      return cuda_fail(c, e, "launch group union solve");
+    sp.cup = c->gcup;
+  }
+  for (uint32_t k = 0; k < n; ++k) {
+    sp.rI[k] = c->gI[k];
+    sp.rU[k] = c->gU[k];
+  }
+  if ((e = launch_group_split(sp, s)) != cudaSuccess) return cuda_fail(c, e, "launch group split");
+  if ((e = cudaMemcpyAsync(c->gerr, c->qerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return cuda_fail(c, e, "group status copy");
+  return SVV_OK;
+}
+
+}  // namespace svv

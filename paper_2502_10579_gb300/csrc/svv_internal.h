@@ -168,6 +168,19 @@ struct CompactArgs {
 
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 
+// result of a query whose source has no out-edge: out[i*V + v] = src_val if
+// v == source else ident for i < L; the same row into rI and rU; row = kNone
+struct IsolatedArgs {
+  uint32_t V, L, source, ident, src_val;
+  uint32_t* out;  // may be null (L = 0)
+  uint32_t* rI;
+  uint32_t* rU;
+  uint32_t* row;
+  uint32_t sms;
+};
+
+cudaError_t launch_isolated(const IsolatedArgs& a, cudaStream_t s);
+
 struct ScatterArgs {
   uint32_t V;
   uint32_t s0, ls;
@@ -232,11 +245,64 @@ struct BatchArgs {
   uint32_t skip_same;               // per-chunk last-relaxed value skip in the solves
 };
 
+// ---------------------------------------------------------------------------
+// Query groups: the bound solves of up to kGroupMax same-type queries in one
+// set of frontier rounds (svv_group.cuh).  Lane k of a group is query k; its
+// values sit at val[v * KL + k] (KL = 4 or 8 lanes per row).
+constexpr int kGroupMax = 8;
+
+struct GroupArgs {
+  DevGraph g;
+  uint32_t nlanes;                 // queries in the group (lanes >= nlanes stay inert)
+  uint32_t source[kGroupMax];
+  int init;                        // kInitSource (intersection) or kInitSeed (union)
+  const uint32_t* base;            // kInitSeed: the intersection rows [V * KL]
+  uint32_t* val;                   // [V * KL] result rows
+  const uint32_t* nflanes;         // [NF] lane word of each partial edge, row order
+  const uint32_t* iplanes;         // [NF] lane word of each partial in-edge, transposed order
+  uint32_t* stamp;                 // [V]
+  unsigned long long* q0;
+  unsigned long long* q1;
+  uint32_t qcap;
+  uint32_t cshift;
+  TeamCtl* ctl;
+  uint32_t* qerr;
+  uint32_t maxit;
+  unsigned long long spin_ns;
+  uint32_t pull_units, push_verts;  // direction switch, as in SolveArgs
+  unsigned long long* trace;
+  uint32_t trace_cap;
+};
+
+// lane words of the partial edges: bit k = lane k's window holds the edge in
+// every snapshot, bit 16 + k = in at least one
+struct LanesArgs {
+  DevGraph g;
+  uint32_t nlanes;
+  Window win[kGroupMax];
+  uint32_t* nflanes;
+  uint32_t* iplanes;  // may be null (no transposed graph)
+};
+
+// per-lane planar copies of the group's bound rows, for the per-query phases
+struct SplitArgs {
+  uint32_t V, nlanes, KL;
+  const uint32_t* cap;
+  const uint32_t* cup;
+  uint32_t* rI[kGroupMax];
+  uint32_t* rU[kGroupMax];
+};
+
 // launch helpers (defined in the .cu files)
 struct LaunchCfg {
   int blocks;     // cooperative grid size
   int threads;
 };
+
+cudaError_t launch_group_lanes(const LanesArgs& a, cudaStream_t s);
+cudaError_t launch_group_solve(int type, uint32_t KL, int pred, const GroupArgs& a, LaunchCfg cfg, cudaStream_t s);
+cudaError_t launch_group_split(const SplitArgs& a, cudaStream_t s);
+int occupancy_group(int threads);
 
 cudaError_t launch_batch(const BatchArgs& b, LaunchCfg cfg, cudaStream_t s);
 int occupancy_batch(int threads);

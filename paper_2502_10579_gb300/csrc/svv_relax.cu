@@ -19,6 +19,8 @@
 // intersection graph, whose values are already a fixed point on it, so it is
 // skipped.  Sources of seed edges hold their intersection-graph value in every
 // snapshot at that point.
+#include <algorithm>
+
 #include "svv_relax.cuh"
 
 namespace svv {
@@ -52,49 +54,64 @@ __device__ __forceinline__ uint32_t pick4(const uint4& w, uint32_t k) {
 
 __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(ScatterArgs a) {
   extern __shared__ __align__(16) uint32_t tile[];  // [ls][kTV], swizzled
-  __shared__ uint32_t s_row[kTV], s_x[kTV];
+  __shared__ uint32_t s_row[kTV];
+  __shared__ __align__(16) uint32_t s_x[kTV];
   if (*a.qerr != 0u) return;
   const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t v0 = blockIdx.x * kTV;
-  const uint32_t nv = min((uint32_t)kTV, a.V - v0);
   const uint32_t lps = __ffs(a.LP) - 1;
-  for (uint32_t t = threadIdx.x; t < (uint32_t)kTV; t += blockDim.x) {
-    const bool in = t < nv;
-    s_row[t] = in ? a.row[v0 + t] : kNone;
-    s_x[t] = in ? a.rI[v0 + t] : 0u;
-  }
-  __syncthreads();
-  for (uint32_t t0 = 4u * wid; t0 < (uint32_t)kTV; t0 += 4u * nw) {
-    uint32_t r[4], x[4];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      r[h] = s_row[t0 + h];
-      x[h] = s_x[t0 + h];
+  const bool vec = (a.V & 3u) == 0u && ((uintptr_t)a.out & 15u) == 0u;
+  constexpr uint32_t kQ = kTV / 4, kRows = kScatterThreads / kQ;  // 16-byte stores: 32 per tile row
+  const uint32_t q = threadIdx.x % kQ, r0 = threadIdx.x / kQ;
+  {
+    const uint32_t tl = blockIdx.x;  // one tile per CTA
+    const uint32_t v0 = tl * kTV;
+    const uint32_t nv = min((uint32_t)kTV, a.V - v0);
+    bool mine = false;
+    for (uint32_t t = threadIdx.x; t < (uint32_t)kTV; t += blockDim.x) {
+      const bool in = t < nv;
+      const uint32_t r = in ? a.row[v0 + t] : kNone;
+      s_row[t] = r;
+      s_x[t] = in ? a.rI[v0 + t] : 0u;
+      mine |= r != kNone;
     }
-    for (uint32_t i = lane; i < a.ls; i += 32u) {
-      uint32_t y[4];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) y[h] = r[h] == kNone ? x[h] : a.val[((size_t)r[h] << lps) + i];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) tile[i * kTV + ((t0 + h) ^ (i & 31u))] = y[h];
+    if (!__syncthreads_or(mine) && vec && nv == (uint32_t)kTV) {
+      // every vertex of the tile is stable: each snapshot row is the tile's
+      // intersection values, written straight from the row map's buffer
+      const uint4 x = *reinterpret_cast<const uint4*>(s_x + 4u * q);
+      for (uint32_t i = r0; i < a.ls; i += kRows)
+        __stcs(reinterpret_cast<uint4*>(a.out + (size_t)(a.s0 + i) * a.V + v0) + q, x);
+      return;
     }
-  }
-  __syncthreads();
-  if ((a.V & 3u) == 0u && nv == (uint32_t)kTV && ((uintptr_t)a.out & 15u) == 0u) {
-    // a warp per tile row: 32 threads x 16 bytes
-    constexpr uint32_t kQ = kTV / 4, kRows = kScatterThreads / kQ;
-    const uint32_t q = threadIdx.x % kQ, r0 = threadIdx.x / kQ;
-    for (uint32_t i = r0; i < a.ls; i += kRows) {
-      const uint32_t sw = i & 31u;
-      const uint4 w = *reinterpret_cast<const uint4*>(tile + i * kTV + 4u * (q ^ (sw >> 2)));
-      const uint32_t k = sw & 3u;
-      const uint4 o = make_uint4(pick4(w, k), pick4(w, 1u ^ k), pick4(w, 2u ^ k), pick4(w, 3u ^ k));
-      __stcs(reinterpret_cast<uint4*>(a.out + (size_t)(a.s0 + i) * a.V + v0) + q, o);
+    for (uint32_t t0 = 4u * wid; t0 < (uint32_t)kTV; t0 += 4u * nw) {
+      uint32_t r[4], x[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        r[h] = s_row[t0 + h];
+        x[h] = s_x[t0 + h];
+      }
+      for (uint32_t i = lane; i < a.ls; i += 32u) {
+        uint32_t y[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) y[h] = r[h] == kNone ? x[h] : a.val[((size_t)r[h] << lps) + i];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) tile[i * kTV + ((t0 + h) ^ (i & 31u))] = y[h];
+      }
     }
-  } else {
-    for (uint32_t i = wid; i < a.ls; i += nw)
-      for (uint32_t t = lane; t < nv; t += 32u)
-        a.out[(size_t)(a.s0 + i) * a.V + v0 + t] = tile[i * kTV + (t ^ (i & 31u))];
+    __syncthreads();
+    if (vec && nv == (uint32_t)kTV) {
+      // a warp per tile row: 32 threads x 16 bytes
+      for (uint32_t i = r0; i < a.ls; i += kRows) {
+        const uint32_t sw = i & 31u;
+        const uint4 w = *reinterpret_cast<const uint4*>(tile + i * kTV + 4u * (q ^ (sw >> 2)));
+        const uint32_t k = sw & 3u;
+        const uint4 o = make_uint4(pick4(w, k), pick4(w, 1u ^ k), pick4(w, 2u ^ k), pick4(w, 3u ^ k));
+        __stcs(reinterpret_cast<uint4*>(a.out + (size_t)(a.s0 + i) * a.V + v0) + q, o);
+      }
+    } else {
+      for (uint32_t i = wid; i < a.ls; i += nw)
+        for (uint32_t t = lane; t < nv; t += 32u)
+          a.out[(size_t)(a.s0 + i) * a.V + v0 + t] = tile[i * kTV + (t ^ (i & 31u))];
+    }
   }
 }
 
@@ -114,6 +131,43 @@ __global__ void __launch_bounds__(256) compact_kernel(CompactArgs a) {
     const uint32_t r = (uint32_t)(k / a.ls), i = (uint32_t)(k % a.ls);
     a.rows_out[(size_t)r * a.wl + a.s0 + i] = a.val[((size_t)r << lps) + i];
   }
+}
+
+// The result of a query from a source with no out-edge, written at the
+// output's bandwidth: 16-byte streaming stores when V is a multiple of 4.
+__global__ void __launch_bounds__(256) isolated_kernel(IsolatedArgs a) {
+  const size_t nthreads = (size_t)gridDim.x * blockDim.x;
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (size_t v = tid; v < a.V; v += nthreads) {
+    const uint32_t x = v == a.source ? a.src_val : a.ident;
+    a.rI[v] = x;
+    a.rU[v] = x;
+    a.row[v] = kNone;
+  }
+  if (!a.out) return;
+  if ((a.V & 3u) == 0u && ((uintptr_t)a.out & 15u) == 0u) {
+    const size_t per_row = a.V >> 2, n = per_row * a.L;
+    for (size_t k = tid; k < n; k += nthreads) {
+      const uint32_t v = (uint32_t)(k % per_row) * 4u;
+      uint4 o = make_uint4(a.ident, a.ident, a.ident, a.ident);
+      if (a.source - v < 4u) {
+        const uint32_t j = a.source - v;
+        if (j == 0) o.x = a.src_val;
+        else if (j == 1) o.y = a.src_val;
+        else if (j == 2) o.z = a.src_val;
+        else o.w = a.src_val;
+      }
+      __stcs(reinterpret_cast<uint4*>(a.out) + k, o);
+    }
+  } else {
+    const size_t n = (size_t)a.V * a.L;
+    for (size_t k = tid; k < n; k += nthreads) a.out[k] = (k % a.V) == a.source ? a.src_val : a.ident;
+  }
+}
+
+cudaError_t launch_isolated(const IsolatedArgs& a, cudaStream_t s) {
+  isolated_kernel<<<std::max<uint32_t>(1, a.sms) * 8u, 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s) {
@@ -159,9 +213,10 @@ cudaError_t launch_relax(int type, uint32_t P, uint32_t K, const RelaxArgs& a, L
 }
 
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
-  const uint32_t blocks = (a.V + kTV - 1) / kTV;
+  const uint32_t blocks = (a.V + kTV - 1) / kTV;  // one tile per CTA
   const size_t smem = (size_t)a.ls * kTV * sizeof(uint32_t);  // up to 64 KB at 128 snapshots
-  if (smem > 48 * 1024) {
+  // the opt-in covers the dynamic tile plus the kernel's static row map
+  if (smem + 2 * kTV * sizeof(uint32_t) > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute((const void*)scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

@@ -1,0 +1,142 @@
+"""Query groups: the bound solves of up to eight same-type queries run as one
+set of frontier rounds (one value lane per query), then each query's own
+phases run from its lane.  Every output must equal the CPU oracle (and the
+same query run alone), whatever the group size, the mix of windows and
+sources, with and without pull rounds, and for the degenerate groups (one
+source for every lane, isolated sources, one-snapshot windows)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def svv():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_10579_gb300 import svv as mod
+    assert torch.cuda.is_available()
+    return mod
+
+
+def _specs(log, n, seed, types=(0, 1, 2, 3), hubs=None):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        L = int(rng.integers(1, log.S + 1))
+        b = int(rng.integers(0, log.S - L + 1))
+        src = int(hubs[k % len(hubs)]) if hubs is not None else int(rng.integers(0, log.V))
+        out.append((types[k % len(types)], src, b, L))
+    return out
+
+
+def _hubs(log, n):
+    deg = np.bincount(log.src[: log.n_base].astype(np.int64), minlength=log.V)
+    return np.argsort(-deg, kind="stable")[:n]
+
+
+def _run(svv, ctx, specs, gmax):
+    ctx.set_tuning("batch_mode", 2)
+    ctx.set_tuning("group_max", gmax)
+    outs, st = ctx.query_batch(specs)
+    assert st == [0] * len(specs)
+    return outs
+
+
+@pytest.mark.parametrize("gmax", [2, 4, 8])
+def test_group_two_words_matches_oracle(svv, gmax):
+    log = W.scaled_rmat(scale=12, edge_factor=8, n_snapshots=100, rate=0.003, seed=31, add_mode="skewed")
+    specs = _specs(log, 26, 5 + gmax, hubs=_hubs(log, 9))
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        outs = _run(svv, ctx, specs, gmax)
+        for (t, s, b, L), o in zip(specs, outs):
+            np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L))
+
+
+@pytest.mark.parametrize("pull", [1, 0])
+def test_group_hubs_equal_alone(svv, pull):
+    """Deep solves from hub sources (pull rounds when the frontier is large,
+    or push only without the transposed graph)."""
+    log = W.scaled_rmat(scale=15, edge_factor=16, n_snapshots=64, rate=0.0005, seed=41)
+    specs = _specs(log, 24, 9, types=(0, 1, 2), hubs=_hubs(log, 12))
+    with svv.Context(0) as ctx:
+        ctx.set_tuning("pull", pull)
+        ctx.load_log(log)
+        outs = _run(svv, ctx, specs, 8)
+        alone = ctx.empty_out(log.S)
+        for (t, s, b, L), o in zip(specs, outs):
+            ctx.query(t, s, b, L, out=alone[:L])
+            assert torch.equal(o, alone[:L])
+        for (t, s, b, L), o in list(zip(specs, outs))[:3]:
+            np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L))
+
+
+def test_group_degenerate_lanes(svv):
+    """One source and window in every lane; isolated sources; windows of one
+    snapshot; the whole history; a group of the largest size next to a group
+    of one."""
+    log = W.small_rmat()
+    deg = np.bincount(log.src.astype(np.int64), minlength=log.V)
+    iso = int(np.flatnonzero(deg == 0)[0])
+    hub = int(_hubs(log, 1)[0])
+    specs = [(0, hub, 0, log.S)] * 8 + [(1, iso, 3, 1), (1, hub, 2, 1), (1, iso, 0, log.S)] + \
+            [(2, hub, 0, 1), (2, hub, 7, 1)] + [(3, hub, 1, 5)]
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        outs = _run(svv, ctx, specs, 8)
+        for (t, s, b, L), o in zip(specs, outs):
+            np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L))
+
+
+def test_group_without_pruning(svv):
+    """The no-pruning ablation (every vertex relaxed) through groups."""
+    log = W.scaled_rmat(scale=11, edge_factor=8, n_snapshots=16, rate=0.01, seed=53)
+    specs = _specs(log, 12, 3, hubs=_hubs(log, 4))
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        ctx.set_tuning("prune", 0)
+        outs = _run(svv, ctx, specs, 4)
+        for (t, s, b, L), o in zip(specs, outs):
+            np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L))
+
+
+def test_group_host_outputs(svv):
+    """Grouped instances with results in page-locked host memory."""
+    log = W.scaled_rmat(scale=12, edge_factor=8, n_snapshots=40, rate=0.003, seed=61)
+    specs = _specs(log, 10, 4, types=(0, 2), hubs=_hubs(log, 5))
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        ctx.set_tuning("group_max", 8)
+        hosts = [torch.empty((L, log.V), dtype=torch.int32, pin_memory=True) for (_, _, _, L) in specs]
+        st = svv.svv_query_batch(ctx.h, [(t, s, b, L, h) for (t, s, b, L), h in zip(specs, hosts)])
+        assert st == [0] * len(specs)
+        for (t, s, b, L), h in zip(specs, hosts):
+            np.testing.assert_array_equal(h.numpy().view(np.uint32), oracle.query(log, t, s, b, L))
+
+
+def test_group_bfs_levels_many_sources(svv):
+    """BFS groups over many random sources on a larger graph, where a vertex
+    can be in one lane's frontier while another lane's level of it is set in
+    the same round; every level must still equal the query run alone."""
+    log = W.scaled_rmat(scale=17, edge_factor=16, n_snapshots=64, rate=0.0005, seed=71)
+    rng = np.random.default_rng(2)
+    deg = np.bincount(log.src[: log.n_base].astype(np.int64), minlength=log.V)
+    cand = np.flatnonzero(deg > 0)
+    specs = []
+    for k in range(24):
+        L = int(rng.integers(8, 65))
+        b = int(rng.integers(0, log.S - L + 1))
+        specs.append((2, int(cand[rng.integers(0, cand.size)]), b, L))
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        outs = _run(svv, ctx, specs, 8)
+        for (t, s, b, L), o in zip(specs, outs):
+            assert torch.equal(o, ctx.query(t, s, b, L))
+        for (t, s, b, L), o in list(zip(specs, outs))[:2]:
+            np.testing.assert_array_equal(svv.to_u32(o)[[0, L - 1]],
+                                          np.stack([oracle.query(log, t, s, b, 1)[0], oracle.query(log, t, s, b + L - 1, 1)[0]]))

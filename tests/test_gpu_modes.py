@@ -118,3 +118,32 @@ def test_load_time_knobs_exact(env2, knobs):
         ctx.load_log(log)
         for t in (0, 1, 2, 3):
             np.testing.assert_array_equal(svv.to_u32(ctx.query(t, src, 5, 80)), _oracle(log, t, src, 5, 80))
+
+
+@pytest.mark.parametrize("t", [0, 1, 2, 3])
+def test_isolated_source_fast_path(env, t):
+    """A source with no out-edge in any snapshot is answered by one fill: the
+    result, the bounds (svv_get_bounds) and the compact form must equal the
+    oracle and the full pipeline (isolated_fast = 0)."""
+    svv, log, ctx = env
+    deg = np.bincount(log.src.astype(np.int64), minlength=log.V)
+    iso = int(np.flatnonzero(deg == 0)[0])
+    for b, L in [(0, 40), (11, 1), (5, 31)]:
+        want = oracle.query(log, t, iso, b, L)
+        fast = svv.to_u32(ctx.query(t, iso, b, L))
+        np.testing.assert_array_equal(fast, want)
+        cap, cup, row = ctx.bounds()
+        ocap, ocup = oracle.bounds(log, t, iso, b, L)
+        np.testing.assert_array_equal(cap, ocap)
+        np.testing.assert_array_equal(cup, ocup)
+        assert (row == INF).all() and ctx.stats()["unstable"] == 0
+        ctx.set_tuning("isolated_fast", 0)
+        try:
+            np.testing.assert_array_equal(svv.to_u32(ctx.query(t, iso, b, L)), want)
+        finally:
+            ctx.set_tuning("isolated_fast", 1)
+        capt = torch.empty(log.V, dtype=torch.int32, device="cuda:0")
+        rowt = torch.empty(log.V, dtype=torch.int32, device="cuda:0")
+        rows = torch.empty(4, dtype=torch.int32, device="cuda:0")
+        assert svv.svv_query_compact(ctx.h, t, iso, b, L, capt, rowt, rows) == 0
+        np.testing.assert_array_equal(svv.to_u32(capt), ocap)

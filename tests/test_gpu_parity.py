@@ -154,6 +154,28 @@ def test_medium_two_words(svv, medium, t):
     np.testing.assert_array_equal(_plain(svv, ctx, t, src, 40, 24), oracle.query(log, t, src, 40, 24))
 
 
+def test_every_window_length(svv, medium):
+    """Every window length 1..100 once (the output tile, the relaxation rows
+    and the mask words change size at different lengths; 95 and 96 snapshots
+    once put the tile just past the default shared-memory limit)."""
+    log, ctx = medium
+    src = W.max_out_degree_vertex(log)
+    rng = np.random.default_rng(5)
+    out = ctx.empty_out(log.S)
+    for L in range(1, log.S + 1):
+        b = int(rng.integers(0, log.S - L + 1))
+        t = TYPES[L % len(TYPES)]
+        ctx.query(t, src, b, L, out=out[:L])
+        got = svv.to_u32(out[:L])
+        # the first and last snapshot against the oracle (every snapshot for
+        # the lengths where a size changes)
+        if L in (1, 63, 64, 65, 94, 95, 96, 97, 100):
+            np.testing.assert_array_equal(got, oracle.query(log, t, src, b, L))
+        else:
+            for i in (0, L - 1):
+                np.testing.assert_array_equal(got[i], oracle.query(log, t, src, b + i, 1)[0])
+
+
 def test_long_window_slabs(svv):
     # windows longer than one 128-snapshot slab
     log = W.scaled_rmat(scale=10, edge_factor=8, n_snapshots=300, rate=0.004, seed=5)
