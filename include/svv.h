@@ -180,15 +180,23 @@ svv_status svv_query_batch(svv_ctx *ctx, uint32_t n, svv_query_spec *specs, void
  * results are released -- that is the admission control.  The kernel leaves
  * after an idle period and is relaunched by the next svv_submit or svv_poll.
  * That is the mode below 2M vertices.  From 2M vertices ("batch_mode" as set
- * when the server starts: 0 = by graph size, 1 = live kernel, 2 = in order),
- * where one request already fills the GPU, svv_submit queues the request's
- * svv_query kernels on the library stream behind the earlier ones, framed by
- * two one-thread marker launches that write its times, status and completion
- * flag to the same mapped memory; requests then run one after another, each
- * on the whole GPU.  In that mode the server shares svv_query's scratch:
- * svv_query, svv_query_compact, svv_query_plain, svv_query_batch and
- * svv_get_bounds on another stream are ordered after the requests submitted
- * before them (stream waits, no host wait), and later requests after them.
+ * when the server starts: 0 = by graph size, 1 = live kernel, 2 = groups),
+ * where one request already fills the GPU, requests run in QUERY GROUPS
+ * (continuous batching): a scheduler thread of the library takes the
+ * submitted requests in arrival order and, each time the group queued last
+ * has finished its bound solves, queues the next group on the library stream
+ * -- up to "group_max" pending requests of the oldest request's type, whose
+ * intersection- and union-graph solves share one set of frontier rounds
+ * (svv_query_batch), then each member's own phases -- framed by one-thread
+ * marker launches that write each request's times, status and completion
+ * flag to the same mapped memory.  Requests that arrive while a group runs
+ * join the next group, so their work overlaps on the device.  A request whose
+ * source has no out-edge is answered alone by one fill.  In that mode the
+ * server shares svv_query's scratch: svv_query, svv_query_compact,
+ * svv_query_plain, svv_query_batch and svv_get_bounds on another stream wait
+ * (without blocking the host) for the groups already queued, and the groups
+ * queued later wait for them; a request still waiting for its group may run
+ * after such a call.
  * max_window bounds win_len; capacity is the number of requests that may be
  * submitted and not yet released.  SVV_ENOMEM if the team scratch (or, in
  * order, the query scratch for max_window) or the arena does not fit the
@@ -227,7 +235,7 @@ svv_status svv_serve_replay(svv_ctx *ctx, uint32_t n, const svv_query_spec *spec
                             const double *arrival_s, double *latency_ms, double *done_s);
 
 /* Stop the server and free its memory (live mode abandons pending requests;
- * in order, the call waits for the queued ones). */
+ * in groups, the call first runs the submitted ones and waits for them). */
 svv_status svv_serve_stop(svv_ctx *ctx);
 
 /* svv_query without the dense output (the paper keeps one result array per

@@ -455,9 +455,12 @@ svv_status svv_load(svv_ctx* c, uint32_t V, uint64_t E, uint32_t S, const uint64
   cudaDeviceSynchronize();
   free_graph(c);
   if (c->budget_auto) {
+    // free memory less a margin and the local memory the driver reserves when
+    // the batch kernel first runs (its stack frames)
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
-    c->budget = fr > (512ull << 20) ? fr - (512ull << 20) : fr / 2;
+    const uint64_t keep = (512ull << 20) + batch_local_bytes(c->device);
+    c->budget = fr > keep ? fr - keep : fr / 2;
   }
   DevGraph g{};
   g.V = V;
@@ -957,12 +960,6 @@ svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, con
 
 svv_status reserve_window(svv_ctx* c, uint32_t L) { return ensure_window(c, L); }
 
-// One request of an in-order server: svv_query's kernels, no host wait.
-svv_status enqueue_instance(svv_ctx* c, const BatchInstance& q, cudaStream_t s) {
-  float a = 0.f, b = 0.f;
-  return enqueue_query(c, q.type, q.source, q.wb, q.wl, q.out, s, false, &a, &b);
-}
-
 }  // namespace svv
 
 extern "C" {
@@ -972,9 +969,9 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
   svv_status st = check_query(c, (int)type, source, wb, wl, out);
   if (st) return st;
   DeviceGuard dg(c->device);
-  if ((st = ensure_window(c, wl))) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  ServeFence fence(c, s);
+  ServeFence fence(c, s);  // before any scratch is resized
+  if ((st = ensure_window(c, wl))) return st;
   const int t = (int)type;
   bool timing = c->phase_timing;
   float ms_relax = 0.f, ms_scatter = 0.f;
@@ -1022,9 +1019,9 @@ svv_status svv_query_compact(svv_ctx* c, svv_type type, uint32_t source, uint32_
   if (st) return st;
   if (!cap_out || !row_out) return fail(c, SVV_EINVAL, "cap_out and row_out are required");
   DeviceGuard dg(c->device);
-  if ((st = ensure_window(c, wl))) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  ServeFence fence(c, s);
+  ServeFence fence(c, s);  // before any scratch is resized
+  if ((st = ensure_window(c, wl))) return st;
   const CompactOut co{cap_out, row_out, rows_out, rows_cap};
   float a = 0.f, b = 0.f;
   if ((st = enqueue_query(c, (int)type, source, wb, wl, nullptr, s, false, &a, &b, &co))) return st;

@@ -240,6 +240,20 @@ cudaError_t launch_batch(const BatchArgs& b, LaunchCfg cfg, cudaStream_t s) {
   return cudaLaunchCooperativeKernel((const void*)batch_kernel, dim3(cfg.blocks), dim3(cfg.threads), args, 0, s);
 }
 
+// Local memory the driver reserves for the batch kernel's stack frames when it
+// first runs: the frame of every thread the device can hold at once.
+uint64_t batch_local_bytes(int device) {
+  cudaFuncAttributes fa{};
+  int sms = 0, per_sm = 0;
+  if (cudaFuncGetAttributes(&fa, (const void*)batch_kernel) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, device) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (uint64_t)fa.localSizeBytes * (uint64_t)per_sm * (uint64_t)sms;
+}
+
 int occupancy_batch(int threads) {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)batch_kernel, threads, 0) != cudaSuccess)

@@ -182,6 +182,7 @@ svv_status status_of(uint32_t qerr, uint32_t done) {
   if (!done) return SVV_ETIMEOUT;
   if (qerr == 0) return SVV_OK;
   if (qerr == kErrTimeout) return SVV_ETIMEOUT;
+  if (qerr == SVV_ECUDA || qerr == SVV_ENOMEM) return (svv_status)qerr;  // the serving scheduler's failures
   return SVV_EINTERNAL;
 }
 

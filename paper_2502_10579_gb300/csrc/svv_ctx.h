@@ -3,8 +3,12 @@
 #pragma once
 
 #include <algorithm>
+#include <condition_variable>
 #include <deque>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/svv.h"
@@ -65,6 +69,22 @@ struct ServeSlot {
   uint32_t* out = nullptr;
 };
 
+// Grouped serving (graphs from 2M vertices): a scheduler thread takes the
+// submitted requests, forms query groups and queues them on the server's
+// stream; `enq` serialises that with every other use of the query scratch.
+struct ServeSched {
+  std::thread th;
+  std::mutex mu;                 // pending, stop
+  std::condition_variable cv;
+  std::deque<uint32_t> pending;  // ring slots submitted and not yet queued
+  bool stop = false;             // drain the pending requests, then leave
+  std::mutex enq;
+  uint32_t *h_gflag = nullptr, *d_gflag = nullptr;  // per queued group: bounds done
+  uint32_t gring = 256;
+  uint64_t gcount = 0;           // groups queued
+  uint64_t grouped = 0;          // requests that ran in a group of two or more
+};
+
 struct ServeState {
   bool active = false;
   uint32_t cap = 0, maxL = 0;
@@ -92,9 +112,11 @@ struct ServeState {
   std::vector<void*> bufs;
   uint64_t bytes = 0;
   unsigned long long idle_ns = 200000000ull;
-  // in-order mode: each request runs svv_query's kernels on `stream`
+  // grouped mode: requests run in query groups queued by the scheduler on
+  // `stream`, with svv_query's scratch
   bool in_order = false;
   cudaEvent_t ord = nullptr;  // orders other streams' use of the query scratch
+  std::unique_ptr<ServeSched> sched;
 };
 
 }  // namespace svv
@@ -106,6 +128,7 @@ struct svv_ctx {
   uint64_t allocated = 0;
   int num_sms = 0;
   std::string err;
+  std::thread::id worker;  // the serving scheduler's thread, while it runs
 
   // tuning
   uint32_t maxit = 0;
@@ -205,7 +228,9 @@ struct svv_ctx {
 namespace svv {
 
 inline svv_status fail(svv_ctx* c, svv_status s, const std::string& msg) {
-  if (c) c->err = msg;
+  // the serving scheduler's failures reach the caller through the request's
+  // status; only the caller's own thread writes the message
+  if (c && std::this_thread::get_id() != c->worker) c->err = msg;
   return s;
 }
 
@@ -307,7 +332,6 @@ svv_status status_of(uint32_t qerr, uint32_t done);
 svv_status check_spec(const svv_ctx* c, const svv_query_spec& q);
 bool batch_one_launch(const svv_ctx* c);
 svv_status reserve_window(svv_ctx* c, uint32_t L);
-svv_status enqueue_instance(svv_ctx* c, const BatchInstance& q, cudaStream_t s);
 
 // While an in-order server is active it shares the single-query scratch: a
 // call that uses that scratch on another stream is ordered after the requests
@@ -316,6 +340,7 @@ struct ServeFence {
   svv_ctx* c;
   cudaStream_t s;
   bool on;
+  std::unique_lock<std::mutex> lk;  // the scheduler's queueing lock while the call runs
   ServeFence(svv_ctx* c, cudaStream_t s);
   ~ServeFence();
 };

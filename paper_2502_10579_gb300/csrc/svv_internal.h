@@ -306,6 +306,7 @@ int occupancy_group(int threads);
 
 cudaError_t launch_batch(const BatchArgs& b, LaunchCfg cfg, cudaStream_t s);
 int occupancy_batch(int threads);
+uint64_t batch_local_bytes(int device);
 
 cudaError_t launch_solve(int type, int pred, const SolveArgs& a, LaunchCfg cfg, cudaStream_t s);
 cudaError_t launch_qrs(const QrsArgs& a, LaunchCfg cfg, cudaStream_t s);

@@ -2,10 +2,17 @@
 //
 // Two modes, chosen like svv_query_batch's: below 2M vertices the batch
 // kernel runs in live mode (below); from 2M vertices, where one request's
-// rounds fill the GPU, each request is queued on the library stream as
-// svv_query's kernels between two one-thread marker launches that write its
-// start time, and its status, end time and completion flag, into the same
-// mapped memory the live kernel uses -- so svv_poll and admission are shared.
+// rounds fill the GPU, requests run in QUERY GROUPS (continuous batching): a
+// scheduler thread takes the submitted requests in arrival order and, each
+// time the group queued last has finished its bound solves, queues the next
+// group -- up to group_max pending requests of the oldest request's type --
+// on the server's stream: one pair of group solves for the members' bounds
+// (one value lane per request, one set of frontier rounds), then each
+// member's own phases.  Requests that arrive while a group runs join the next
+// one, so their work overlaps on the device in the shared rounds.  One-thread
+// marker launches write each request's start time, status, end time and
+// completion flag into mapped memory, so svv_poll and admission are the same
+// in both modes.
 //
 // Live mode: the batch kernel runs on a library stream.  svv_submit writes
 // the request into a ring of instances in host-mapped pinned memory and raises
@@ -40,9 +47,16 @@ __global__ void serve_mark_kernel(const uint32_t* qerr, uint32_t* qerr_out, uint
   }
 }
 
+// Groups set this flag when their bound solves are done.
+__global__ void serve_flag_kernel(uint32_t* flag) {
+  __threadfence_system();
+  *reinterpret_cast<volatile uint32_t*>(flag) = 1u;
+}
+
 ServeFence::ServeFence(svv_ctx* c_, cudaStream_t s_) : c(c_), s(s_), on(false) {
   ServeState& v = c->serve;
   if (!v.active || !v.in_order || s == v.stream) return;
+  if (v.sched) lk = std::unique_lock<std::mutex>(v.sched->enq);  // no group is queued meanwhile
   if (cudaEventRecord(v.ord, v.stream) == cudaSuccess && cudaStreamWaitEvent(s, v.ord, 0) == cudaSuccess) on = true;
   else cudaStreamSynchronize(v.stream);
 }
@@ -56,6 +70,18 @@ ServeFence::~ServeFence() {
 
 void free_serve(svv_ctx* c) {
   ServeState& v = c->serve;
+  if (v.sched) {
+    if (v.sched->th.joinable()) {
+      {
+        std::lock_guard<std::mutex> g(v.sched->mu);
+        v.sched->stop = true;
+      }
+      v.sched->cv.notify_all();
+      v.sched->th.join();
+    }
+    c->worker = std::thread::id();
+    if (v.sched->h_gflag) cudaFreeHost(v.sched->h_gflag);
+  }
   if (v.stream) {
     if (v.h_ctrl) {
       reinterpret_cast<volatile uint32_t*>(v.h_ctrl)[1] = 1u;
@@ -90,6 +116,112 @@ svv_status host_mapped(svv_ctx* c, uint64_t n, T** h, T** d) {
   std::memset(*h, 0, n * sizeof(T));
   if (cudaHostGetDevicePointer((void**)d, *h, 0) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "mapped pointer");
   return SVV_OK;
+}
+
+// Queue one group (or one request) on the server's stream.  Members that
+// cannot be queued are completed at once with the failure as their status.
+void queue_group(svv_ctx* c, const std::vector<uint32_t>& grp) {
+  ServeState& v = c->serve;
+  ServeSched& S = *v.sched;
+  cudaStream_t st = v.stream;
+  const uint32_t gslot = (uint32_t)(S.gcount % S.gring);
+  reinterpret_cast<volatile uint32_t*>(S.h_gflag)[gslot] = 0u;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  S.gcount++;
+  std::vector<bool> marked(grp.size(), false);
+  svv_status bad = SVV_OK;
+  for (uint32_t slot : grp) serve_mark_kernel<<<1, 1, 0, st>>>(nullptr, nullptr, nullptr, v.d_t0 + slot);
+  if (cudaGetLastError() != cudaSuccess) bad = SVV_ECUDA;
+  float a = 0.f, b = 0.f;
+  if (!bad && grp.size() > 1) {
+    BatchInstance gi[kGroupMax];
+    for (size_t j = 0; j < grp.size(); ++j) gi[j] = v.h_inst[grp[j]];
+    bad = enqueue_group_bounds(c, gi[0].type, gi, (uint32_t)grp.size(), st);
+    if (!bad) {
+      serve_flag_kernel<<<1, 1, 0, st>>>(S.d_gflag + gslot);
+      if (cudaGetLastError() != cudaSuccess) bad = SVV_ECUDA;
+    }
+    for (size_t j = 0; j < grp.size() && !bad; ++j) {
+      const BatchInstance& q = gi[j];
+      const uint32_t slot = grp[j];
+      if (cudaMemcpyAsync(c->qerr, c->gerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        bad = SVV_ECUDA;
+        break;
+      }
+      if ((bad = enqueue_tail(c, q.type, q.wb, q.wl, q.out, c->gI[j], c->gU[j], st, false, &a, &b, nullptr, true)))
+        break;
+      serve_mark_kernel<<<1, 1, 0, st>>>(c->qerr, v.d_qerr + slot, v.d_done + slot, v.d_t1 + slot);
+      if (cudaGetLastError() != cudaSuccess) bad = SVV_ECUDA;
+      else marked[j] = true;
+    }
+    if (!bad) S.grouped += grp.size();
+  } else if (!bad) {
+    const uint32_t slot = grp[0];
+    const BatchInstance& q = v.h_inst[slot];
+    bad = enqueue_query(c, q.type, q.source, q.wb, q.wl, q.out, st, false, &a, &b);
+    if (!bad) {
+      serve_flag_kernel<<<1, 1, 0, st>>>(S.d_gflag + gslot);
+      serve_mark_kernel<<<1, 1, 0, st>>>(c->qerr, v.d_qerr + slot, v.d_done + slot, v.d_t1 + slot);
+      if (cudaGetLastError() != cudaSuccess) bad = SVV_ECUDA;
+      else marked[0] = true;
+    }
+  }
+  if (bad) {
+    cudaGetLastError();
+    cudaStreamSynchronize(st);  // what was queued has finished; then report the rest
+    for (size_t j = 0; j < grp.size(); ++j) {
+      if (marked[j]) continue;
+      reinterpret_cast<volatile uint32_t*>(v.h_qerr)[grp[j]] = (uint32_t)bad;
+      std::atomic_thread_fence(std::memory_order_seq_cst);
+      reinterpret_cast<volatile uint32_t*>(v.h_done)[grp[j]] = 1u;
+    }
+    reinterpret_cast<volatile uint32_t*>(S.h_gflag)[gslot] = 1u;
+  }
+}
+
+// The scheduler: forms a group whenever the previous one has its bounds.
+void sched_loop(svv_ctx* c) {
+  ServeState& v = c->serve;
+  ServeSched& S = *v.sched;
+  cudaSetDevice(c->device);
+  std::unique_lock<std::mutex> lk(S.mu);
+  for (;;) {
+    if (S.pending.empty()) {
+      if (S.stop) break;
+      S.cv.wait_for(lk, std::chrono::milliseconds(2));
+      continue;
+    }
+    if (S.gcount > 0 && !reinterpret_cast<volatile uint32_t*>(S.h_gflag)[(S.gcount - 1) % S.gring]) {
+      // the last group is still solving its bounds: let requests gather
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(10));
+      lk.lock();
+      continue;
+    }
+    std::vector<uint32_t> grp;
+    const uint32_t first = S.pending.front();
+    const BatchInstance q0 = v.h_inst[first];
+    if (c->group_max <= 1 || source_is_isolated(c, q0.source)) {
+      grp.push_back(first);
+      S.pending.pop_front();
+    } else {
+      for (auto it = S.pending.begin(); it != S.pending.end() && grp.size() < c->group_max;) {
+        const BatchInstance& q = v.h_inst[*it];
+        if (q.type == q0.type && !source_is_isolated(c, q.source)) {
+          grp.push_back(*it);
+          it = S.pending.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    lk.unlock();
+    {
+      std::lock_guard<std::mutex> g(S.enq);
+      queue_group(c, grp);
+    }
+    lk.lock();
+  }
 }
 
 svv_status launch_live(svv_ctx* c) {
@@ -198,6 +330,7 @@ svv_status svv_serve_start(svv_ctx* c, uint32_t max_window, uint32_t capacity, u
   ServeState& v = c->serve;
   v.in_order = !batch_one_launch(c);
   svv_status st = v.in_order ? reserve_window(c, max_window) : ensure_pool(c, default_teams(c), max_window);
+  if (!st && v.in_order) st = ensure_group(c);
   if (st) return st;
   v.cap = capacity;
   v.maxL = max_window;
@@ -231,6 +364,25 @@ svv_status svv_serve_start(svv_ctx* c, uint32_t max_window, uint32_t capacity, u
     return cuda_fail(c, e, "serve start");
   }
   v.slots.assign(capacity, ServeSlot{});
+  if (v.in_order) {
+    v.sched.reset(new (std::nothrow) ServeSched());
+    if (!v.sched) {
+      free_serve(c);
+      return fail(c, SVV_ENOMEM, "serving scheduler");
+    }
+    if ((st = host_mapped(c, v.sched->gring, &v.sched->h_gflag, &v.sched->d_gflag))) {
+      free_serve(c);
+      return st;
+    }
+    v.active = true;
+    try {
+      v.sched->th = std::thread(sched_loop, c);
+    } catch (...) {
+      free_serve(c);
+      return fail(c, SVV_ENOMEM, "could not start the serving scheduler");
+    }
+    c->worker = v.sched->th.get_id();
+  }
   v.active = true;
   c->err.clear();
   return SVV_OK;
@@ -261,18 +413,12 @@ svv_status svv_submit(svv_ctx* c, const svv_query_spec* spec, uint64_t* ticket) 
   reinterpret_cast<volatile uint32_t*>(v.h_qerr)[slot] = 0u;
   reinterpret_cast<volatile uint32_t*>(v.h_done)[slot] = 0u;
   std::atomic_thread_fence(std::memory_order_seq_cst);
-  if (v.in_order) {
-    serve_mark_kernel<<<1, 1, 0, v.stream>>>(nullptr, nullptr, nullptr, v.d_t0 + slot);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && (st = enqueue_instance(c, v.h_inst[slot], v.stream)) == SVV_OK) {
-      serve_mark_kernel<<<1, 1, 0, v.stream>>>(c->qerr, v.d_qerr + slot, v.d_done + slot, v.d_t1 + slot);
-      e = cudaGetLastError();
+  if (v.in_order) {  // the scheduler queues it with the next group
+    {
+      std::lock_guard<std::mutex> g(v.sched->mu);
+      v.sched->pending.push_back(slot);
     }
-    if (st || e != cudaSuccess) {
-      if (use_arena) arena_free(v, off);
-      s = ServeSlot{};
-      return st ? st : cuda_fail(c, e, "queueing a request");
-    }
+    v.sched->cv.notify_one();
     *ticket = v.tail++;
     c->err.clear();
     return SVV_OK;

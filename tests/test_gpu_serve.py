@@ -91,17 +91,28 @@ def test_serve_admission_and_relaunch(svv):
         svv.svv_serve_stop(ctx.h)
 
 
-def test_serve_in_order(svv):
-    """batch_mode 2: each request is queued as svv_query's kernels on the
-    server's stream; requests run one after another, a query on another stream
-    in between is ordered with them, and admission still refuses a full arena."""
+@pytest.mark.parametrize("gmax", [8, 1])
+def test_serve_groups(svv, gmax):
+    """batch_mode 2 (the mode of graphs from 2M vertices): a scheduler queues
+    the submitted requests in query groups of up to group_max same-type
+    requests, formed each time the previous group has its bounds.  Requests
+    submitted while a group runs share the next group's rounds (their device
+    spans overlap); with group_max 1 they run one after another.  A query on
+    another stream in between is ordered with them, every result equals the
+    query alone, and admission still refuses a full arena."""
     log = W.scaled_rmat(scale=13, edge_factor=8, n_snapshots=100, rate=0.003, seed=56, add_mode="skewed")
-    reqs = _requests(log, 16, 11, 100)
+    deg = np.bincount(log.src.astype(np.int64), minlength=log.V)
+    has_edges = np.flatnonzero(deg > 0)
+    # sources with out-edges (an isolated source is answered alone, by a fill),
+    # plus one isolated source
+    reqs = [(t, int(has_edges[s % has_edges.size]), b, L) for t, s, b, L in _requests(log, 23, 11, 100)]
+    reqs.insert(7, (0, int(np.flatnonzero(deg == 0)[0]), 5, 40))
     with svv.Context(0) as ctx:
         ctx.load_log(log)
         alone = [svv.to_u32(ctx.query(t, s, b, L)) for t, s, b, L in reqs]
         ctx.set_tuning("batch_mode", 2)
-        svv.svv_serve_start(ctx.h, max_window=100, capacity=32, arena_bytes=300 * log.V * 4)
+        ctx.set_tuning("group_max", gmax)
+        svv.svv_serve_start(ctx.h, max_window=100, capacity=64, arena_bytes=900 * log.V * 4)
         side = torch.cuda.Stream()
         pending, spans, refused = [], [], 0
 
@@ -130,7 +141,9 @@ def test_serve_in_order(svv):
             finish_oldest()
         assert refused > 0
         assert all(t0 < t1 for t0, t1 in spans)
-        assert all(spans[i + 1][0] >= spans[i][1] for i in range(len(spans) - 1))  # one after another
+        order = sorted(spans)
+        overlap = any(order[i + 1][0] < order[i][1] for i in range(len(order) - 1))
+        assert overlap == (gmax > 1)  # shared rounds, or one after another
         svv.svv_serve_stop(ctx.h)
         t, s, b, L = reqs[1]
         np.testing.assert_array_equal(alone[1], oracle.query(log, t, s, b, L))
