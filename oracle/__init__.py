@@ -9,8 +9,11 @@ materialised by replaying the edge log (paper Section 2, Fig. 2a): binary-heap
 Dijkstra for SSSP, widest-path Dijkstra for SSWP, a FIFO BFS and narrowest-path
 Dijkstra for SSNP (Table 2).
 ``bounds()`` solves the intersection and union graphs of a window (Section 3,
-Step 1).  Value encoding: SSSP/BFS/SSNP unreachable = 0xFFFFFFFF; SSWP source =
-0xFFFFFFFF (+inf) and unreachable = 0; SSSP sums saturate at 0xFFFFFFFE.
+Step 1).  ``live_intervals()`` and ``window_csr()`` give the same graphs (and
+every snapshot, as a one-snapshot window) from one replay of the log, for
+checks over many windows.  Value encoding: SSSP/BFS/SSNP unreachable =
+0xFFFFFFFF; SSWP source = 0xFFFFFFFF (+inf) and unreachable = 0; SSSP sums
+saturate at 0xFFFFFFFE.
 
 Every function is pinned by ``tests/test_oracle_pins.py`` (Floyd-Warshall
 brute force, SciPy's graph routines, a pure-Python replay, Theorems 1 and 2,
@@ -59,7 +62,11 @@ def _L():
             lib.oracle_snapshot_csr.argtypes = [u32, u32, u64, P, P, P, P, P, P, u32, P,
                                                 ctypes.POINTER(P), ctypes.POINTER(P)]
             lib.oracle_free.argtypes = [P]
-            for f in (lib.oracle_solve, lib.oracle_query, lib.oracle_bounds, lib.oracle_snapshot_csr):
+            lib.oracle_live_intervals.argtypes = [u32, u32, u64, P, P, P, P, P, P, P, P]
+            lib.oracle_window_csr.argtypes = [u32, u32, u64, P, P, P, P, P, u32, u32, i32, P,
+                                              ctypes.POINTER(P), ctypes.POINTER(P)]
+            for f in (lib.oracle_solve, lib.oracle_query, lib.oracle_bounds, lib.oracle_snapshot_csr,
+                      lib.oracle_live_intervals, lib.oracle_window_csr):
                 f.restype = i32
             _lib = lib
     return _lib
@@ -121,6 +128,40 @@ def snapshot_csr(log, snap: int):
     rc = _L().oracle_snapshot_csr(log.V, log.S, a[0].shape[0], *[_p(x) for x in a], snap, _p(rp),
                                   ctypes.byref(cp), ctypes.byref(wp))
     _check(rc, "snapshot_csr")
+    m = int(rp[-1])
+    try:
+        col = np.ctypeslib.as_array(ctypes.cast(cp, ctypes.POINTER(ctypes.c_uint32)), (max(m, 1),))[:m].copy()
+        w = np.ctypeslib.as_array(ctypes.cast(wp, ctypes.POINTER(ctypes.c_uint32)), (max(m, 1),))[:m].copy()
+    finally:
+        _L().oracle_free(cp)
+        _L().oracle_free(wp)
+    return rp, col, w
+
+
+def live_intervals(log):
+    """(t_add, t_del): instance k is live exactly in snapshots [t_add[k], t_del[k]),
+    from one replay of the log's steps (Section 2)."""
+    a = _log_arrays(log)
+    n = a[0].shape[0]
+    t_add = np.empty(max(n, 1), np.uint32)
+    t_del = np.empty(max(n, 1), np.uint32)
+    _check(_L().oracle_live_intervals(log.V, log.S, n, *[_p(x) for x in a], _p(t_add), _p(t_del)), "live_intervals")
+    return t_add[:n], t_del[:n]
+
+
+def window_csr(log, intervals, win_begin: int, win_len: int, kind: str):
+    """CSR ``(row_ptr, col, w)`` of the window's intersection graph
+    (``kind="cap"``: instances live in every window snapshot) or union graph
+    (``kind="cup"``: live in at least one), Section 3 Step 1; a one-snapshot
+    window is that snapshot."""
+    a = _log_arrays(log)
+    t_add, t_del = (np.ascontiguousarray(x, np.uint32) for x in intervals)
+    rp = np.empty(log.V + 1, np.uint64)
+    cp, wp = ctypes.c_void_p(), ctypes.c_void_p()
+    rc = _L().oracle_window_csr(log.V, log.S, a[0].shape[0], _p(a[0]), _p(a[1]), _p(a[2]), _p(t_add), _p(t_del),
+                                win_begin, win_len, {"cap": 0, "cup": 1}[kind], _p(rp), ctypes.byref(cp),
+                                ctypes.byref(wp))
+    _check(rc, "window_csr")
     m = int(rp[-1])
     try:
         col = np.ctypeslib.as_array(ctypes.cast(cp, ctypes.POINTER(ctypes.c_uint32)), (max(m, 1),))[:m].copy()

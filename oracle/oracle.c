@@ -430,3 +430,61 @@ done:
     free(in_any);
     return rc;
 }
+
+/* ------------------------------------------------------------------ */
+/* live intervals: one replay for many windows                          */
+/* ------------------------------------------------------------------ */
+
+/* Snapshot s is the graph after step s (Section 2): the step's deletions,
+ * then its additions.  So instance k is live exactly in the snapshots
+ * [t_add[k], t_del[k]): added in step t_add[k], deleted in step t_del[k]
+ * (S if never deleted; an instance that is never added gets t_add = S, an
+ * empty interval).  One pass over the steps in order records both. */
+int oracle_live_intervals(uint32_t V, uint32_t S, uint64_t n_inst, const uint32_t *src,
+                          const uint32_t *dst, const uint32_t *w, const int64_t *add_off,
+                          const int64_t *del_off, const int64_t *del_ids, uint32_t *t_add,
+                          uint32_t *t_del) {
+    (void)V;
+    (void)src;
+    (void)dst;
+    (void)w;
+    for (uint64_t k = 0; k < n_inst; ++k) {
+        t_add[k] = S;
+        t_del[k] = S;
+    }
+    for (uint32_t s = 0; s < S; ++s) {
+        for (int64_t j = del_off[s]; j < del_off[s + 1]; ++j) {
+            const int64_t k = del_ids[j];
+            if (k < 0 || (uint64_t)k >= n_inst) return -2;
+            t_del[k] = s;
+        }
+        for (int64_t k = add_off[s]; k < add_off[s + 1]; ++k) {
+            if (k < 0 || (uint64_t)k >= n_inst) return -2;
+            t_add[k] = s;
+        }
+    }
+    return 0;
+}
+
+/* CSR of the window [win_begin, win_begin+win_len) as Section 3 Step 1
+ * defines its graphs, from live intervals: kind 0 = the intersection graph
+ * (instances live in every window snapshot: added by win_begin, not deleted
+ * before win_begin+win_len), kind 1 = the union graph (live in at least one
+ * window snapshot).  A window of one snapshot gives that snapshot. */
+int oracle_window_csr(uint32_t V, uint32_t S, uint64_t n_inst, const uint32_t *src,
+                      const uint32_t *dst, const uint32_t *w, const uint32_t *t_add,
+                      const uint32_t *t_del, uint32_t win_begin, uint32_t win_len, int kind,
+                      uint64_t *row_ptr, uint32_t **col, uint32_t **wout) {
+    if (win_len == 0 || (uint64_t)win_begin + win_len > S || (kind != 0 && kind != 1)) return -2;
+    edge_log lg = {V, S, n_inst, src, dst, w, NULL, NULL, NULL};
+    unsigned char *keep = (unsigned char *)malloc(n_inst ? n_inst : 1);
+    if (!keep) return -1;
+    const uint32_t end = win_begin + win_len;
+    for (uint64_t k = 0; k < n_inst; ++k) {
+        if (kind == 0) keep[k] = (unsigned char)(t_add[k] <= win_begin && t_del[k] >= end);
+        else keep[k] = (unsigned char)(t_add[k] < t_del[k] && t_add[k] < end && t_del[k] > win_begin);
+    }
+    int rc = materialise(&lg, keep, row_ptr, col, wout);
+    free(keep);
+    return rc;
+}

@@ -176,6 +176,60 @@ def test_replay_matches_python_sets():
             assert sorted(live) == sorted(alive)
 
 
+def _python_alive(log):
+    """Live instances of every snapshot, replaying the steps with Python sets
+    (Section 2: a step's deletions, then its additions)."""
+    alive, out = set(), []
+    for snap in range(log.S):
+        for k in log.del_ids[log.del_off[snap]:log.del_off[snap + 1]]:
+            alive.discard(int(k))
+        alive.update(range(int(log.add_off[snap]), int(log.add_off[snap + 1])))
+        out.append(set(alive))
+    return out
+
+
+def _triples(log, keep):
+    return sorted((int(log.src[k]), int(log.dst[k]), int(log.w[k])) for k in keep)
+
+
+def _csr_triples(rp, col, w):
+    rows = np.repeat(np.arange(rp.shape[0] - 1), np.diff(rp.astype(np.int64)))
+    return sorted(zip(rows.tolist(), col.tolist(), w.tolist()))
+
+
+def test_live_intervals_match_python_replay():
+    for seed in range(4):
+        log = W.random_small_log(seed, V=40, n_edges=120, S=7, n_add=9, n_del=7)
+        t_add, t_del = oracle.live_intervals(log)
+        for snap, alive in enumerate(_python_alive(log)):
+            assert {k for k in range(log.n_inst) if t_add[k] <= snap < t_del[k]} == alive
+
+
+def test_window_graphs_match_replay():
+    """Every window's intersection / union graph from the intervals equals the
+    intersection / union of the replayed snapshots, a one-snapshot window is
+    the snapshot, and the bounds solved on them are oracle.bounds."""
+    for seed in range(3):
+        log = W.random_small_log(10 + seed, V=30, n_edges=90, S=6, n_add=8, n_del=8)
+        iv = oracle.live_intervals(log)
+        alive = _python_alive(log)
+        rng = np.random.default_rng(seed)
+        for b in range(log.S):
+            for L in range(1, log.S - b + 1):
+                cap_set = set.intersection(*alive[b:b + L])
+                cup_set = set.union(*alive[b:b + L])
+                rp_i, col_i, w_i = oracle.window_csr(log, iv, b, L, "cap")
+                rp_u, col_u, w_u = oracle.window_csr(log, iv, b, L, "cup")
+                assert _csr_triples(rp_i, col_i, w_i) == _triples(log, cap_set)
+                assert _csr_triples(rp_u, col_u, w_u) == _triples(log, cup_set)
+                if L == 1:
+                    assert _csr_triples(*oracle.snapshot_csr(log, b)) == _triples(log, cap_set)
+                qtype, src = int(rng.integers(0, 4)), int(rng.integers(0, log.V))
+                cap, cup = oracle.bounds(log, qtype, src, b, L)
+                np.testing.assert_array_equal(oracle.solve(qtype, log.V, rp_i, col_i, w_i, src), cap)
+                np.testing.assert_array_equal(oracle.solve(qtype, log.V, rp_u, col_u, w_u, src), cup)
+
+
 def _check_theorems(log, qtype, src, b, L):
     vals = oracle.query(log, qtype, src, b, L)
     cap, cup = oracle.bounds(log, qtype, src, b, L)
