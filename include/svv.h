@@ -132,12 +132,33 @@ svv_status svv_load(svv_ctx *ctx, uint32_t V, uint64_t E, uint32_t S, const uint
  * window snapshots, and the scatter into `out`.  `out` is a caller-owned
  * DEVICE buffer of win_len*V uint32 (e.g. a torch tensor).  Work is ordered on
  * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream); the call
- * returns after the stream reaches the end of the query, with its status.
+ * returns after the stream reaches the end of the query, with its status
+ * (svv_query_async returns as soon as the work is queued).
  * On failure `out` holds no valid result (a window of more than 128 snapshots
  * is relaxed and written slab by slab, so earlier slabs may have been written).
  * SVV_EINVAL on type, source >= V, win_len == 0 or win_begin+win_len > S. */
 svv_status svv_query(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
                      uint32_t win_len, uint32_t *out, void *cuda_stream);
+
+/* svv_query without the host wait: the arguments are checked, the query's
+ * kernels are queued on `cuda_stream` and the call returns; *ticket
+ * identifies the query.  `out` is written when the stream reaches the end of
+ * the query (its status, which only the device knows -- a bounded wait that
+ * expired or the round cap -- is read with svv_query_wait).  Queries of one
+ * context share its scratch, so the library orders each one after those
+ * queued before it (stream waits, no host wait), on any stream; every other
+ * call that uses the scratch is ordered after them too.  At most 64 queries
+ * are in flight: queuing a 65th first waits for the oldest.  Diagnostics
+ * (svv_get_stats) are not recorded for these queries.  SVV_EINVAL as
+ * svv_query. */
+svv_status svv_query_async(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
+                           uint32_t win_len, uint32_t *out, void *cuda_stream, uint64_t *ticket);
+
+/* Status of a query queued by svv_query_async: with wait != 0 the call waits
+ * for the query; with wait == 0 it returns SVV_EBUSY while the query runs.
+ * A ticket stays valid until 64 later queries have been queued (then
+ * SVV_EINVAL). */
+svv_status svv_query_wait(svv_ctx *ctx, uint64_t ticket, int wait);
 
 /* Many queries in one call (the instances may mix types, sources and window
  * lengths).  On graphs below 2M vertices the batch runs as ONE persistent
@@ -316,21 +337,33 @@ svv_status svv_solve_snapshot_noalloc(svv_type type, uint32_t V, uint64_t E, uin
 svv_status svv_get_round_trace(svv_ctx *ctx, uint32_t phase, uint64_t *out, uint32_t cap,
                                uint32_t *n_out);
 
-/* Result of svv_autotune: the knobs chosen for one query type. */
+/* Result of svv_autotune: the knobs chosen for one query type and window-
+ * length bucket. */
 typedef struct {
     uint32_t solve_chunk, blocks_per_sm, relax_lanes, skip_same;
+    uint32_t pull_pct;          /* direction switch of the solves (0 = push only) */
+    uint32_t delta;             /* near-far width (SSSP, SSWP; 0 = off) */
+    uint32_t slab_max;          /* snapshots relaxed per pass */
     float best_ms, default_ms;  /* probe query time with the chosen and the default knobs */
     uint32_t candidates;        /* configurations timed */
 } svv_tune_result;
 
-/* Autotuner: times a probe query (type, source, window) under every candidate
- * of a grid of launch knobs -- edges per work unit of the solves (two sizes at
- * or above the loaded one), CTAs per SM (occupancy limit, 2, 3), lanes per
- * edge in the relaxation (32, 16), per-chunk skipping of already-relaxed work
- * (on, off) -- `reps` timed runs each after one warm-up (0 = 3), and keeps the
- * fastest for that query type: later svv_query / svv_query_plain calls of the
- * type use it (results are identical for every candidate).  The probe output
- * goes to a library buffer of win_len*V uint32.  `out` may be NULL. */
+/* Autotuner: times a probe query (type, source, window), `reps` timed runs per
+ * candidate after one warm-up (0 = 3), and keeps the fastest knobs for that
+ * query type and window-length bucket (windows of up to 8, 16, 32, 64 and
+ * more than 64 snapshots).  The search is coordinate descent from the
+ * current defaults, one knob at a time with the others at the best found so
+ * far: the pull threshold of the solves' direction switch (0, 5, 10, 15, 25,
+ * 40 % of all work units), the near-far width (SSSP: 0, 250, 1000, 4000;
+ * SSWP: 0, 50, 200, 800), edges per work unit of the solves (two sizes at or
+ * above the loaded one), CTAs per SM (occupancy limit, 2, 3), lanes per edge in
+ * the relaxation (32, 16), per-chunk skipping of already-relaxed work (on,
+ * off), and for windows over 32 snapshots the slab width (128, 64, 32); a
+ * value is kept when it is more than 2% faster.  Later svv_query,
+ * svv_query_plain, batch and served queries of the type use the knobs of
+ * their bucket (or of the nearest tuned one).  Results are identical for
+ * every candidate.  The probe output goes to a library buffer of win_len*V
+ * uint32.  `out` may be NULL. */
 svv_status svv_autotune(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t win_begin,
                         uint32_t win_len, uint32_t reps, svv_tune_result *out);
 
@@ -350,7 +383,8 @@ svv_status svv_autotune(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t w
  * "graph" (1 = svv_query captures its launches into a CUDA graph, updates the
  * instantiated graph in place for the next query of the same shape and
  * replays it; falls back to direct launches where capture is refused; phase
- * timing is not recorded in this mode),
+ * timing is not recorded in this mode; an in-order svv_query_batch with
+ * device outputs likewise captures all its launches into one graph),
  * "group_max" (1..8, default 8: queries per group of an in-order batch and of
  * the server from 2M vertices; 1 runs every query alone), "group_pull_pct" /
  * "group_pull_pct_union" (0..100, defaults 15 / 100: a group's intersection /
@@ -359,6 +393,10 @@ svv_status svv_autotune(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t w
  * source has no out-edge in any snapshot is answered by one fill -- the
  * source value at the source, unreachable everywhere else -- instead of the
  * full pipeline; 0 runs the pipeline; results are identical),
+ * "test_skip_arrival" (test hook, 0 = off: k+1 makes CTA k of every
+ * intersection-graph solve leave before its first barrier arrival, so the
+ * other CTAs' bounded waits expire after "spin_limit_ms" and the query
+ * returns SVV_ETIMEOUT -- the way to test failure detection without a fault),
  * "batch_teams" (teams of svv_query_batch and the server, 1..64; 0 = by graph
  * size: 8 up to 1M vertices, fewer above, 1 from 8M), "batch_mode" (0 = by
  * graph size, 1 = one launch, 2 = in order; see svv_query_batch), "relax_lanes" (8, 16, 32:

@@ -36,9 +36,21 @@ void free_graph(svv_ctx* c) {
   c->mcap = c->valcap = c->staging_cap = 0;
 }
 
-Knobs knobs_of(const svv_ctx* c, int type) {
-  if (type >= 0 && type < 4 && c->has_tuned[type]) return c->tuned[type];
-  return Knobs{c->solve_cs, c->bps, c->relax_lanes, c->skip_same};
+Knobs default_knobs(const svv_ctx* c, int type) {
+  const uint32_t delta = (type == 0 || type == 1) ? c->delta[type] : 0u;
+  return Knobs{c->solve_cs, c->bps, c->relax_lanes, c->skip_same, c->pull_pct, delta, c->slab_max};
+}
+
+// the knobs the autotuner chose for this type and window length (the nearest
+// tuned length bucket), else the defaults
+Knobs knobs_of(const svv_ctx* c, int type, uint32_t L) {
+  if (type < 0 || type > 3) return default_knobs(c, 0);
+  const int b = len_bucket(L);
+  for (int d = 0; d < kLenBuckets; ++d) {
+    if (b - d >= 0 && c->has_tuned[type][b - d]) return c->tuned[type][b - d];
+    if (b + d < kLenBuckets && c->has_tuned[type][b + d]) return c->tuned[type][b + d];
+  }
+  return default_knobs(c, type);
 }
 
 LaunchCfg cfg_for(const svv_ctx* c, int occ, int bps) {
@@ -52,11 +64,13 @@ svv_status ensure_window(svv_ctx* c, uint32_t L) {
   const uint32_t QW = ceil_div(L, 64);
   const uint64_t need_m = (uint64_t)std::max<uint32_t>(c->g.NF, 1) * QW;
   uint32_t P, K;
-  slab_shape(std::min(L, c->slab_max), P, K);
+  slab_shape(std::min(L, kMaxSlab), P, K);  // any slab width a query of L may use
   const uint64_t need_v = (uint64_t)std::max<uint32_t>(c->g.V, 1) * P * K;
-  // an in-order server's queued requests still read the old buffers
+  // an in-order server's queued requests, or stream-ordered queries, may
+  // still read the old buffers
   if ((need_m > c->mcap || need_v > c->valcap) && c->serve.active && c->serve.stream)
     cudaStreamSynchronize(c->serve.stream);
+  if ((need_m > c->mcap || need_v > c->valcap) && c->async_last) cudaEventSynchronize(c->async_last);
   if (need_m > c->mcap) {
     if (c->qmask) {
       auto it = std::find(c->scratch_bufs.begin(), c->scratch_bufs.end(), (void*)c->qmask);
@@ -107,15 +121,15 @@ SolveArgs solve_base(svv_ctx* c, uint32_t wb, uint32_t wl, int type, const Knobs
   a.qcap = c->qcap;
   a.cshift = kn.solve_cs;
   a.qerr = c->qerr;
-  a.delta = (type == 0 || type == 1) ? c->delta[type] : 0u;
+  a.delta = (type == 0 || type == 1) ? kn.delta : 0u;
   // deferred rounds add to the round count, so the default cap is wider
   const uint64_t cap = a.delta ? 16ull * c->g.V + 64 : (uint64_t)c->g.V + 2;
   a.maxit = c->maxit ? c->maxit : (uint32_t)std::min<uint64_t>(cap, 0xFFFFFFF0ull);
   a.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
-  if (c->g.ifd && c->pull_pct) {
+  if (c->g.ifd && kn.pull_pct) {
     const uint64_t all_units = (uint64_t)c->g.V + (c->g.E >> kn.solve_cs);
-    a.pull_units = (uint32_t)std::max<uint64_t>(1, all_units * c->pull_pct / 100);
-    a.push_verts = (uint32_t)std::max<uint64_t>(1, (uint64_t)c->g.V * c->pull_pct / 100);
+    a.pull_units = (uint32_t)std::max<uint64_t>(1, all_units * kn.pull_pct / 100);
+    a.push_verts = (uint32_t)std::max<uint64_t>(1, (uint64_t)c->g.V * kn.pull_pct / 100);
   }
   if (kn.skip_same && c->procv) {
     a.procv = c->procv;
@@ -220,8 +234,12 @@ void svv_destroy(svv_ctx* c) {
       if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (auto& e : c->aev)
+      if (e) cudaEventDestroy(e);
+    if (c->astatus) cudaFreeHost(c->astatus);
     if (c->trace) cudaFree(c->trace);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->bgexec) cudaGraphExecDestroy(c->bgexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   }
   delete c;
@@ -285,6 +303,9 @@ svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
   } else if (k == "group_pull_pct" || k == "group_pull_pct_union") {
     if (v < 0 || v > 100) return fail(c, SVV_EINVAL, k + " in [0, 100]");
     c->group_pull_pct[k == "group_pull_pct" ? 0 : 1] = (uint32_t)v;
+  } else if (k == "test_skip_arrival") {
+    if (v < 0 || v > 0xFFFF) return fail(c, SVV_EINVAL, "test_skip_arrival in [0, 65535]");
+    c->skip_arrival = (uint32_t)v;
   } else if (k == "isolated_fast") {
     if (v != 0 && v != 1) return fail(c, SVV_EINVAL, "isolated_fast is 0 or 1");
     c->isolated_fast = v != 0;
@@ -617,13 +638,14 @@ svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32
   if (source_is_isolated(c, source)) return enqueue_isolated(c, t, source, wl, out, s, timing, co);
 
   // a1: intersection graph (edges present in every window snapshot)
-  const Knobs kn = knobs_of(c, t);
+  const Knobs kn = knobs_of(c, t, wl);
   SolveArgs a1 = solve_base(c, wb, wl, t, kn);
   a1.init = kInitSource;
   a1.source = source;
   a1.val = c->rI;
   a1.ctl = c->ctl + 0;
   a1.skip_nf = (wb == 0 && wl == c->g.S) ? 1 : 0;
+  a1.skip_arrival = c->skip_arrival;
   if (c->round_trace) {
     cudaMemsetAsync(c->trace, 0, 4 * kTraceCap * sizeof(unsigned long long), s);
     a1.trace = c->trace;
@@ -657,7 +679,7 @@ svv_status enqueue_tail(svv_ctx* c, int t, uint32_t wb, uint32_t wl, uint32_t* o
                         const uint32_t* rU, cudaStream_t s, bool timing, float* ms_relax_out, float* ms_scatter_out,
                         const CompactOut* co, bool fresh) {
   cudaError_t e = cudaSuccess;
-  const Knobs kn = knobs_of(c, t);
+  const Knobs kn = knobs_of(c, t, wl);
   if (fresh && (e = cudaMemsetAsync(c->ctl + 2, 0, sizeof(TeamCtl) * 2, s)) != cudaSuccess)
     return cuda_fail(c, e, "memset");
   c->last_rI = rI;
@@ -694,7 +716,7 @@ svv_status enqueue_tail(svv_ctx* c, int t, uint32_t wb, uint32_t wl, uint32_t* o
   float ms_relax = 0.f, ms_scatter = 0.f;
   // a5+a6 per slab of at most 128 snapshots (a window longer than that is
   // relaxed slab by slab over the same subgraph; snapshots are independent)
-  const uint32_t slab = std::max<uint32_t>(1, std::min(c->slab_max, kMaxSlab));
+  const uint32_t slab = std::max<uint32_t>(1, std::min(kn.slab_max, kMaxSlab));
   for (uint32_t s0 = 0; s0 < wl; s0 += slab) {
     const uint32_t ls = std::min(slab, wl - s0);
     uint32_t P, K;
@@ -905,6 +927,54 @@ svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, con
   // into a staging slot and copied back on the copy stream while the next
   // instance computes; a slot is reused only after its last copy has finished.
   const std::vector<std::vector<uint32_t>> groups = form_groups(c, inst, m, c->group_max);
+  // graph mode (device outputs): the batch's launches are captured into one
+  // CUDA graph, updated in place when the next batch has the same shape, and
+  // launched on `s`; allocations happen before the capture
+  cudaStream_t es = s;
+  bool capture = c->graph_mode && !host_out && !c->round_trace;
+  if (capture) {
+    for (const auto& grp : groups)
+      if (grp.size() > 1 && (st = ensure_group(c))) return st;
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      capture = false;
+    } else if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      capture = false;
+    } else {
+      es = c->cap_stream;
+    }
+  }
+  auto end_capture = [&](svv_status why) -> svv_status {
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &gr);
+    if (why || ec != cudaSuccess || !gr) {
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+      return why ? why : fail(c, SVV_ECUDA, "batch capture failed");
+    }
+    bool ok = false;
+    if (c->bgexec) {
+      cudaGraphExecUpdateResultInfo info;
+      ok = cudaGraphExecUpdate(c->bgexec, gr, &info) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(c->bgexec);
+        c->bgexec = nullptr;
+      }
+    }
+    if (!ok && cudaGraphInstantiate(&c->bgexec, gr, 0) != cudaSuccess) {
+      cudaGetLastError();
+      c->bgexec = nullptr;
+      cudaGraphDestroy(gr);
+      return fail(c, SVV_ECUDA, "batch graph instantiation failed");
+    }
+    cudaGraphDestroy(gr);
+    const cudaError_t el = cudaGraphLaunch(c->bgexec, s);
+    if (el != cudaSuccess) return cuda_fail(c, el, "batch graph launch");
+    c->graph_launches++;
+    return SVV_OK;
+  };
   bool used[2] = {false, false};
   uint32_t nh = 0;
   for (const auto& grp : groups) {
@@ -912,7 +982,8 @@ svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, con
     if (grouped) {
       BatchInstance gi[kGroupMax];
       for (size_t j = 0; j < grp.size(); ++j) gi[j] = inst[grp[j]];
-      if ((st = enqueue_group_bounds(c, gi[0].type, gi, (uint32_t)grp.size(), s))) return st;
+      if ((st = enqueue_group_bounds(c, gi[0].type, gi, (uint32_t)grp.size(), es)))
+        return capture ? end_capture(st) : st;
     }
     for (size_t j = 0; j < grp.size(); ++j) {
       const uint32_t k = grp[j];
@@ -926,16 +997,18 @@ svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, con
         out = c->bstage[slot];
       }
       if (grouped) {
-        if ((e = cudaMemcpyAsync(c->qerr, c->gerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-          return cuda_fail(c, e, "group status copy");
-        if ((st = enqueue_tail(c, inst[k].type, inst[k].wb, inst[k].wl, out, c->gI[j], c->gU[j], s, false, &a, &b,
-                               nullptr, true)))
-          return st;
-      } else if ((st = enqueue_query(c, inst[k].type, inst[k].source, inst[k].wb, inst[k].wl, out, s, false, &a, &b))) {
-        return st;
+        if ((e = cudaMemcpyAsync(c->qerr, c->gerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, es)) != cudaSuccess)
+          st = cuda_fail(c, e, "group status copy");
+        else
+          st = enqueue_tail(c, inst[k].type, inst[k].wb, inst[k].wl, out, c->gI[j], c->gU[j], es, false, &a, &b,
+                            nullptr, true);
+      } else {
+        st = enqueue_query(c, inst[k].type, inst[k].source, inst[k].wb, inst[k].wl, out, es, false, &a, &b);
       }
-      if ((e = cudaMemcpyAsync(qerr_dev + k, c->qerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return cuda_fail(c, e, "batch status copy");
+      if (!st && (e = cudaMemcpyAsync(qerr_dev + k, c->qerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, es)) !=
+                     cudaSuccess)
+        st = cuda_fail(c, e, "batch status copy");
+      if (st) return capture ? end_capture(st) : st;
       if (slot >= 0) {
         const size_t bytes = (size_t)inst[k].wl * c->g.V * sizeof(uint32_t);
         e = cudaEventRecord(c->ev_done[slot], s);
@@ -948,6 +1021,7 @@ svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, con
       }
     }
   }
+  if (capture && (st = end_capture(SVV_OK))) return st;
   cudaEventRecord(c->bev[1], s);
   e = cudaMemcpyAsync(qerr_host, qerr_dev, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1001,7 +1075,7 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
     cudaEventElapsedTime(&S.ms_cap, c->ev[0], c->ev[1]);
     cudaEventElapsedTime(&S.ms_cup, c->ev[1], c->ev[2]);
     cudaEventElapsedTime(&S.ms_qrs, c->ev[2], c->ev[3]);
-    if (wl > std::max<uint32_t>(1, std::min(c->slab_max, kMaxSlab))) {
+    if (wl > std::max<uint32_t>(1, std::min(knobs_of(c, t, wl).slab_max, kMaxSlab))) {
       S.ms_relax = ms_relax;
       S.ms_scatter = ms_scatter;
     } else {
@@ -1010,6 +1084,60 @@ svv_status svv_query(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, ui
     }
   }
   return st;
+}
+
+svv_status svv_query_async(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, uint32_t wl, uint32_t* out,
+                           void* stream, uint64_t* ticket) {
+  svv_status st = check_query(c, (int)type, source, wb, wl, out);
+  if (st) return st;
+  if (!ticket) return fail(c, SVV_EINVAL, "ticket is NULL");
+  DeviceGuard dg(c->device);
+  cudaError_t e = cudaSuccess;
+  if (!c->astatus) {
+    if ((e = cudaMallocHost((void**)&c->astatus, sizeof(uint32_t) * kAsyncSlots)) != cudaSuccess) {
+      c->astatus = nullptr;
+      return cuda_fail(c, e, "status ring");
+    }
+    for (auto& ev : c->aev)
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(c, e, "cudaEventCreate");
+  }
+  const uint32_t slot = (uint32_t)(c->anext % kAsyncSlots);
+  // the ring holds kAsyncSlots queries: the oldest must be done before its
+  // slot is reused
+  if (c->anext >= (uint64_t)kAsyncSlots && (e = cudaEventSynchronize(c->aev[slot])) != cudaSuccess)
+    return cuda_fail(c, e, "waiting for the oldest query");
+  cudaStream_t s = (cudaStream_t)stream;
+  ServeFence fence(c, s);  // after the queries queued before, before any scratch is resized
+  if ((st = ensure_window(c, wl))) return st;
+  float a = 0.f, b = 0.f;
+  if ((st = enqueue_query(c, (int)type, source, wb, wl, out, s, false, &a, &b))) return st;
+  if ((e = cudaMemcpyAsync(c->astatus + slot, c->qerr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaEventRecord(c->aev[slot], s)) != cudaSuccess)
+    return cuda_fail(c, e, "queueing the query's status");
+  c->async_last = c->aev[slot];
+  *ticket = c->anext++;
+  c->err.clear();
+  return SVV_OK;
+}
+
+svv_status svv_query_wait(svv_ctx* c, uint64_t ticket, int wait) {
+  if (!c) return SVV_EINVAL;
+  if (ticket >= c->anext) return fail(c, SVV_EINVAL, "unknown ticket");
+  if (c->anext - ticket > (uint64_t)kAsyncSlots)
+    return fail(c, SVV_EINVAL, "ticket expired: more than 64 queries were queued after it");
+  DeviceGuard dg(c->device);
+  const uint32_t slot = (uint32_t)(ticket % kAsyncSlots);
+  cudaError_t e = wait ? cudaEventSynchronize(c->aev[slot]) : cudaEventQuery(c->aev[slot]);
+  if (e == cudaErrorNotReady) {
+    cudaGetLastError();
+    return SVV_EBUSY;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "query");
+  const uint32_t q = reinterpret_cast<volatile uint32_t*>(c->astatus)[slot];
+  if (q == kErrTimeout) return fail(c, SVV_ETIMEOUT, "a device wait or the round cap expired");
+  if (q != 0) return fail(c, SVV_EINTERNAL, "device capacity check failed");
+  return SVV_OK;
 }
 
 svv_status svv_query_compact(svv_ctx* c, svv_type type, uint32_t source, uint32_t wb, uint32_t wl,
@@ -1051,13 +1179,13 @@ svv_status svv_query_plain(svv_ctx* c, svv_type type, uint32_t source, uint32_t 
     TeamCtl* slot = c->ctl + 8 + (i % (kNumCtl - 8));
     if (i >= (uint32_t)(kNumCtl - 8) && (e = cudaMemsetAsync(slot, 0, sizeof(TeamCtl), s)) != cudaSuccess)
       return cuda_fail(c, e, "memset");
-    SolveArgs a = solve_base(c, wb, wl, (int)type, knobs_of(c, (int)type));
+    SolveArgs a = solve_base(c, wb, wl, (int)type, knobs_of(c, (int)type, wl));
     a.init = kInitSource;
     a.source = source;
     a.bit = wb + i;
     a.val = out + (size_t)i * c->g.V;
     a.ctl = slot;
-    if ((e = launch_solve((int)type, kPredBit, a, cfg_for(c, c->occ_solve, knobs_of(c, (int)type).bps), s)) !=
+    if ((e = launch_solve((int)type, kPredBit, a, cfg_for(c, c->occ_solve, knobs_of(c, (int)type, wl).bps), s)) !=
         cudaSuccess)
       return cuda_fail(c, e, "launch per-snapshot solve");
   }

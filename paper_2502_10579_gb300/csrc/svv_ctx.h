@@ -16,7 +16,8 @@
 
 namespace svv {
 
-constexpr int kNumCtl = 8 + 256;  // 0..3 query phases, 8.. per-snapshot plain solves
+constexpr int kNumCtl = 8 + 256;  // 0..3 query phases, 4..5 group solves, 8.. per-snapshot plain solves
+constexpr int kAsyncSlots = 64;   // svv_query_async queries in flight
 constexpr uint32_t kMaxSlab = 128;
 constexpr uint32_t kTraceCap = 4096;
 
@@ -52,13 +53,21 @@ struct BatchPool {
   uint64_t ibytes = 0;
 };
 
-// launch knobs of one query type (the autotuner picks them per type)
+// launch knobs of one query type and window-length bucket (the autotuner
+// picks them; the defaults come from svv_set_tuning)
 struct Knobs {
   uint32_t solve_cs;
   int bps;
   uint32_t relax_lanes;
   bool skip_same;
+  uint32_t pull_pct;  // pull when the frontier holds more than this % of all units (0 = push only)
+  uint32_t delta;     // near-far width of the SSSP / SSWP solves (0 = off)
+  uint32_t slab_max;  // snapshots relaxed per pass
 };
+constexpr int kLenBuckets = 5;  // windows of up to 8, 16, 32, 64, 128+ snapshots
+inline int len_bucket(uint32_t L) {
+  return L <= 8 ? 0 : L <= 16 ? 1 : L <= 32 ? 2 : L <= 64 ? 3 : 4;
+}
 
 // serving: instance ring in host-mapped memory, output arena, live kernel
 struct ServeSlot {
@@ -189,11 +198,12 @@ struct svv_ctx {
   bool graph_mode = false;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t bgexec = nullptr;  // the last in-order batch, captured
   uint64_t graph_builds = 0, graph_launches = 0;
 
   // per-type knobs chosen by svv_autotune
-  svv::Knobs tuned[4] = {};
-  bool has_tuned[4] = {false, false, false, false};
+  svv::Knobs tuned[4][svv::kLenBuckets] = {};
+  bool has_tuned[4][svv::kLenBuckets] = {};
 
   // batched queries
   svv::BatchPool batch;
@@ -215,9 +225,16 @@ struct svv_ctx {
   uint32_t *gcap = nullptr, *gcup = nullptr, *gnfl = nullptr, *gipl = nullptr, *gerr = nullptr;
   uint32_t* gI[svv::kGroupMax] = {};
   uint32_t* gU[svv::kGroupMax] = {};
+  // stream-ordered queries (svv_query_async): a ring of completion events
+  // and page-locked status words; the latest one orders later scratch users
+  cudaEvent_t aev[svv::kAsyncSlots] = {};
+  uint32_t* astatus = nullptr;
+  uint64_t anext = 0;
+  cudaEvent_t async_last = nullptr;
   // host copy of each vertex's out-degree over edges present in some snapshot
   std::vector<uint32_t> hdeg;
   bool isolated_fast = true;  // answer queries from a source without out-edges by one fill
+  uint32_t skip_arrival = 0;  // test hook of the bounded barrier waits (see SolveArgs)
   // bounds the last query's phases read (svv_get_bounds)
   const uint32_t* last_rI = nullptr;
   const uint32_t* last_rU = nullptr;
@@ -304,7 +321,8 @@ struct CompactOut {
   uint32_t* rows_out;
   uint64_t rows_cap;
 };
-Knobs knobs_of(const svv_ctx* c, int type);
+Knobs default_knobs(const svv_ctx* c, int type);
+Knobs knobs_of(const svv_ctx* c, int type, uint32_t L);
 LaunchCfg cfg_for(const svv_ctx* c, int occ, int bps);
 SolveArgs solve_base(svv_ctx* c, uint32_t wb, uint32_t wl, int type, const Knobs& kn);
 svv_status enqueue_query(svv_ctx* c, int t, uint32_t source, uint32_t wb, uint32_t wl, uint32_t* out,

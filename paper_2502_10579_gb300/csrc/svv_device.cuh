@@ -27,6 +27,19 @@ __device__ __forceinline__ unsigned long long ld_cg(const unsigned long long* p)
 // write of the earlier rounds.
 __device__ __forceinline__ uint32_t ld_val(const uint32_t* p) { return *p; }
 
+// Read-only loads of data streamed once per pass (the edge arrays of a pull
+// round): no L1 allocation, so the pass leaves L1 to the value gathers.
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream(const uint2* p) {
+  uint2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

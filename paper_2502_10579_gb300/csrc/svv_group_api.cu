@@ -45,7 +45,7 @@ svv_status enqueue_group_bounds(svv_ctx* c, int t, const BatchInstance* inst, ui
   svv_status st = ensure_group(c);
   if (st) return st;
   const uint32_t KL = n <= 4 ? 4u : 8u;
-  const Knobs kn = knobs_of(c, t);
+  const Knobs kn = knobs_of(c, t, inst[0].wl);
   cudaError_t e = cudaMemsetAsync(c->ctl + 4, 0, sizeof(TeamCtl) * 2, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->qerr, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "memset");

@@ -99,6 +99,9 @@ struct SolveArgs {
   // in-edges; after a pull round that changed more than push_verts vertices the
   // next round pulls again.  0 disables pulling.
   uint32_t pull_units, push_verts;
+  // test hook (0 = off): CTA skip_arrival-1 leaves before its first barrier
+  // arrival, so the other CTAs' bounded waits expire (SVV_ETIMEOUT)
+  uint32_t skip_arrival;
 };
 
 struct QrsArgs {

@@ -54,6 +54,8 @@ __global__ void serve_flag_kernel(uint32_t* flag) {
 }
 
 ServeFence::ServeFence(svv_ctx* c_, cudaStream_t s_) : c(c_), s(s_), on(false) {
+  // stream-ordered queries still in flight use the same scratch
+  if (c->async_last) cudaStreamWaitEvent(s, c->async_last, 0);
   ServeState& v = c->serve;
   if (!v.active || !v.in_order || s == v.stream) return;
   if (v.sched) lk = std::unique_lock<std::mutex>(v.sched->enq);  // no group is queued meanwhile

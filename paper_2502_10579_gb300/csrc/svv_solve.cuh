@@ -41,6 +41,7 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
   // no chunk has been relaxed yet: the identity is never a queued value
   if (a.procv)
     for (uint32_t k = gtid; k < a.pcap; k += nthreads) a.procv[k] = Op::kIdentity;
+  if (a.skip_arrival && t.rank + 1u == a.skip_arrival) return false;  // test hook: never arrives
   if (!t.sync()) return false;
   if (a.trace && gtid == 0 && a.trace_cap) a.trace[0] = global_ns() & 0xFFFFFFFFFFull;
 
@@ -145,7 +146,7 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
           d[j] = 0xFFFFFFFFu - lane;  // unique per lane when not live
           src[j] = 0;
           w[j] = 0;
-          if (live[j]) d[j] = idx < EF ? __ldg(g.ifd + idx) : __ldg(g.ipd + (idx - EF));
+          if (live[j]) d[j] = idx < EF ? ld_stream(g.ifd + idx) : ld_stream(g.ipd + (idx - EF));
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -153,7 +154,7 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
           if (live[j] && bottom_up && ld_val(a.val + d[j]) != kInf) live[j] = false;
           if (live[j]) {
             if (idx < EF) {
-              const uint2 sw = __ldg(g.ifcw + idx);
+              const uint2 sw = ld_stream(g.ifcw + idx);
               src[j] = sw.x;
               w[j] = sw.y;
             } else {
@@ -163,7 +164,7 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
               if (PRED == kPredAll) present = window_all(m, a.win);
               else if (PRED == kPredAny) present = window_any(m, a.win);
               else present = mask_bit(m, a.bit);
-              const uint2 sw = __ldg(g.ipcw + k);
+              const uint2 sw = ld_stream(g.ipcw + k);
               src[j] = sw.x;
               w[j] = sw.y;
               live[j] = present;

@@ -25,7 +25,7 @@ EXPORTS = ("svv_create", "svv_build_versioned_csr", "svv_load", "svv_query", "sv
            "svv_last_error", "svv_destroy", "svv_solve_snapshot_noalloc",
            "svv_get_round_trace", "svv_query_batch", "svv_serve_start", "svv_submit", "svv_poll",
            "svv_ticket_info", "svv_release", "svv_serve_stop", "svv_serve_replay", "svv_autotune",
-           "svv_query_compact")
+           "svv_query_compact", "svv_query_async", "svv_query_wait")
 
 
 class SvvError(RuntimeError):
@@ -42,6 +42,7 @@ class svv_query_spec(ctypes.Structure):
 class svv_tune_result(ctypes.Structure):
     _fields_ = [("solve_chunk", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("relax_lanes", ctypes.c_uint32), ("skip_same", ctypes.c_uint32),
+                ("pull_pct", ctypes.c_uint32), ("delta", ctypes.c_uint32), ("slab_max", ctypes.c_uint32),
                 ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float), ("candidates", ctypes.c_uint32)]
 
 
@@ -104,6 +105,10 @@ def lib():
     L.svv_autotune.restype = i32
     L.svv_query_compact.argtypes = [P, i32, u32, u32, u32, P, P, P, u64, ctypes.POINTER(u32), P]
     L.svv_query_compact.restype = i32
+    L.svv_query_async.argtypes = [P, i32, u32, u32, u32, P, P, ctypes.POINTER(u64)]
+    L.svv_query_async.restype = i32
+    L.svv_query_wait.argtypes = [P, u64, i32]
+    L.svv_query_wait.restype = i32
     for f in ("svv_serve_start", "svv_submit", "svv_poll", "svv_ticket_info", "svv_release", "svv_serve_stop",
               "svv_serve_replay"):
         getattr(L, f).restype = i32
@@ -203,6 +208,23 @@ def svv_load(ctx, V: int, E: int, S: int, row_ptr, col, weight, mask, inputs_on_
 
 def svv_query(ctx, qtype: int, source: int, win_begin: int, win_len: int, out, stream=None):
     _check(ctx, lib().svv_query(ctx, qtype, source, win_begin, win_len, _ptr(out), _stream(stream)))
+
+
+def svv_query_async(ctx, qtype: int, source: int, win_begin: int, win_len: int, out, stream=None) -> int:
+    """Queue a query on the stream and return its ticket (no host wait)."""
+    t = ctypes.c_uint64()
+    _check(ctx, lib().svv_query_async(ctx, qtype, source, win_begin, win_len, _ptr(out), _stream(stream),
+                                      ctypes.byref(t)))
+    return int(t.value)
+
+
+def svv_query_wait(ctx, ticket: int, wait: bool = True):
+    """The status of a queued query (raises on failure), or None while it runs (wait=False)."""
+    st = lib().svv_query_wait(ctx, ticket, 1 if wait else 0)
+    if st == 5:
+        return None
+    _check(ctx, st)
+    return 0
 
 
 def svv_query_plain(ctx, qtype: int, source: int, win_begin: int, win_len: int, out, stream=None):

@@ -1,15 +1,26 @@
 """Parity at the full sizes of the measured workloads, in the launch
-configuration bench.py times, on outputs sampled so the oracle finishes:
+configuration bench.py times, on outputs the oracle can recompute one by one:
 
-* RMAT scale 24, 100 snapshots (two mask words): SSSP and BFS at windows of 25,
-  50 and 100 from several sources; the first and last snapshot of every window
-  against the oracle.
-* RMAT scale 22, 64 snapshots: the 256-query mixed batch in one launch; every
-  instance equal to the same query alone, and sampled snapshots of several
-  instances equal to the oracle.
-* RMAT scale 22, 128 snapshots: requests served while others run equal the
-  same queries alone.
+* RMAT scale 22, 64 snapshots, the 256-query mixed batch in one
+  svv_query_batch call (query groups): every query's first and last snapshot
+  and every snapshot of four queries against the oracle; every query's bounds
+  (svv_get_bounds after the query alone) equal to the oracle's bounds; every
+  snapshot of every output inside the bounds of Theorem 1 / Table 1 and equal
+  to the bound on the stable vertices (Theorem 2); every output equal to the
+  same query alone.
+* RMAT scale 24, 100 snapshots (two mask words): the 96 SSSP and BFS queries
+  (16 sources x windows of 25, 50, 100), the same checks.
+* RMAT scale 22, 128 snapshots: requests served while others run (query
+  groups), the same checks, and every result equal to the query alone.
+
+The oracle work is spread over the host cores: each graph an oracle solve
+needs (a snapshot, or a window's intersection or union graph) is built once
+from the log's live intervals and shared by the solves on it.
 """
+import os
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -18,6 +29,9 @@ import workloads as W
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+INF = 0xFFFFFFFF
+WORKERS = max(1, os.cpu_count() or 1)
 
 
 @pytest.fixture(scope="module")
@@ -36,62 +50,206 @@ def _load(svv, log):
     return ctx
 
 
-def _check_sampled(svv, log, ctx, q, out):
-    got = svv.to_u32(out[: q.win_len])
-    for i in sorted({0, q.win_len - 1}):
-        want = oracle.query(log, q.type, q.source, q.win_begin + i, 1)[0]
-        np.testing.assert_array_equal(got[i], want)
+class OracleSolves:
+    """Oracle solves over many graphs of one log, in parallel on the host while
+    the GPU works.
+
+    A graph key is ("cap", b, L) or ("cup", b, L) (a window's intersection or
+    union graph; ("cap", i, 1) is snapshot i).  Each graph is built once and
+    freed when its last solve is done; solves run on every core but one."""
+
+    def __init__(self, log):
+        self.log = log
+        self.iv = oracle.live_intervals(log)
+        self.want = {}  # key -> set of (type, source)
+
+    def need(self, key, qtype, source):
+        self.want.setdefault(key, set()).add((int(qtype), int(source)))
+
+    def start(self):
+        graphs, left, locks, self.out = {}, {}, {}, {}
+        guard = threading.Lock()
+        tasks = [(k, t, s) for k in sorted(self.want) for t, s in sorted(self.want[k])]
+        for k in self.want:
+            left[k] = len(self.want[k])
+            locks[k] = threading.Lock()
+
+        def task(item):
+            key, t, s = item
+            with locks[key]:
+                if key not in graphs:
+                    graphs[key] = oracle.window_csr(self.log, self.iv, key[1], key[2], key[0])
+                g = graphs[key]
+            val = oracle.solve(t, self.log.V, *g, s)
+            with guard:
+                self.out[(key, t, s)] = val
+                left[key] -= 1
+                if left[key] == 0:
+                    graphs.pop(key, None)
+
+        self.pool = ThreadPoolExecutor(max(1, WORKERS - 1))
+        self.futures = [self.pool.submit(task, it) for it in tasks]
+        return self
+
+    def result(self):
+        for f in self.futures:
+            f.result()
+        self.pool.shutdown()
+        return self.out
 
 
-def test_rmat24_sampled(svv):
-    log = W.rmat24()
-    qs = W.rmat24_queries(log)
-    ctx = _load(svv, log)
-    try:
-        out = ctx.empty_out(max(q.win_len for q in qs))
-        sample = [qs[0], qs[-1]]  # SSSP at L=25, BFS at L=100 (each Dijkstra at this size takes ~20 s)
-        for q in sample:
-            ctx.query(q.type, q.source, q.win_begin, q.win_len, out=out[: q.win_len])
-            _check_sampled(svv, log, ctx, q, out)
-    finally:
-        ctx.close()
+def _u64(x):
+    """uint32 values held in an int32 tensor, as int64 for ordered compares."""
+    return x.to(torch.int64) & 0xFFFFFFFF
+
+
+def _check_invariants(out, cap, cup, qtype):
+    """Theorem 1 / Table 1: every snapshot lies between the union-graph and the
+    intersection-graph values (reversed for SSWP); Theorem 2: a vertex whose
+    bounds agree has that value in every snapshot.  On the device."""
+    o = _u64(out)
+    c = _u64(torch.from_numpy(cap.view(np.int32)).to(out.device))[None]
+    u = _u64(torch.from_numpy(cup.view(np.int32)).to(out.device))[None]
+    lo, hi = (c, u) if qtype == oracle.SSWP else (u, c)
+    assert bool(((o >= lo) & (o <= hi)).all())
+    stable = (c == u)
+    assert bool(((o == c) | ~stable).all())
+
+
+def _plan(solves, qs, full):
+    """First and last snapshot of every query, every snapshot of the queries in
+    `full`, and both bounds of every query."""
+    for i, q in enumerate(qs):
+        snaps = range(q.win_len) if i in full else sorted({0, q.win_len - 1})
+        for k in snaps:
+            solves.need(("cap", q.win_begin + k, 1), q.type, q.source)
+        solves.need(("cap", q.win_begin, q.win_len), q.type, q.source)
+        solves.need(("cup", q.win_begin, q.win_len), q.type, q.source)
+
+
+def _full_set(qs, deg, n=4):
+    """Four queries whose sources reach something, of as many types as there
+    are, shortest windows first (every snapshot is recomputed)."""
+    order = sorted((q.win_len, i) for i, q in enumerate(qs) if deg[q.source] > 0)
+    picked, types = [], set()
+    for _, i in order:
+        if qs[i].type not in types:
+            picked.append(i)
+            types.add(qs[i].type)
+        if len(picked) == n:
+            break
+    for _, i in order:
+        if len(picked) == n:
+            break
+        if i not in picked:
+            picked.append(i)
+    return set(picked)
+
+
+def _verify(svv, ctx, log, qs, outs, want, full):
+    """Compare each query's GPU output with the oracle values in `want`."""
+    for i, (q, o) in enumerate(zip(qs, outs)):
+        snaps = range(q.win_len) if i in full else sorted({0, q.win_len - 1})
+        for k in snaps:
+            got = o[k].cpu().numpy().view(np.uint32)
+            np.testing.assert_array_equal(got, want[(("cap", q.win_begin + k, 1), q.type, q.source)],
+                                          err_msg=f"query {i} snapshot {q.win_begin + k}")
+        cap = want[(("cap", q.win_begin, q.win_len), q.type, q.source)]
+        cup = want[(("cup", q.win_begin, q.win_len), q.type, q.source)]
+        _check_invariants(o, cap, cup, q.type)
 
 
 def test_rmat22_batch_full(svv):
     log = W.rmat22()
     qs = W.batch_queries(log, n=256, seed=3)
+    deg = np.bincount(log.src.astype(np.int64), minlength=log.V)
+    full = _full_set(qs, deg)
+    solves = OracleSolves(log)
+    _plan(solves, qs, full)
+    solves.start()
     ctx = _load(svv, log)
     try:
         outs = [ctx.empty_out(q.win_len) for q in qs]
         st = svv.svv_query_batch(ctx.h, [(q.type, q.source, q.win_begin, q.win_len, o) for q, o in zip(qs, outs)])
         assert st == [0] * len(qs)
-        alone = ctx.empty_out(64)
+        bounds = []
         for q, o in zip(qs, outs):
-            ctx.query(q.type, q.source, q.win_begin, q.win_len, out=alone[: q.win_len])
-            assert torch.equal(o, alone[: q.win_len])
-        for q, o in list(zip(qs, outs))[:3]:
-            _check_sampled(svv, log, ctx, q, o)
+            alone = ctx.query(q.type, q.source, q.win_begin, q.win_len)
+            assert torch.equal(o, alone)
+            bounds.append(ctx.bounds()[:2])
+        want = solves.result()
+        _verify(svv, ctx, log, qs, outs, want, full)
+        for q, (cap, cup) in zip(qs, bounds):
+            np.testing.assert_array_equal(cap, want[(("cap", q.win_begin, q.win_len), q.type, q.source)])
+            np.testing.assert_array_equal(cup, want[(("cup", q.win_begin, q.win_len), q.type, q.source)])
     finally:
         ctx.close()
 
 
-def test_rmat22_served_equals_alone(svv):
+def test_rmat24_full(svv):
+    log = W.rmat24()
+    qs = W.rmat24_queries(log)
+    # every snapshot of the 25-snapshot windows of the first two sources
+    full = {i for i, q in enumerate(qs[:12]) if q.win_len == 25}
+    assert len(full) == 4
+    solves = OracleSolves(log)
+    _plan(solves, qs, full)
+    solves.start()
+    ctx = _load(svv, log)
+    try:
+        # the GPU results while the oracle runs: the sampled snapshots and the
+        # bounds to the host, the invariants checked once the oracle is done
+        out = ctx.empty_out(max(q.win_len for q in qs))
+        got = []
+        for i, q in enumerate(qs):
+            o = out[: q.win_len]
+            ctx.query(q.type, q.source, q.win_begin, q.win_len, out=o)
+            snaps = range(q.win_len) if i in full else sorted({0, q.win_len - 1})
+            got.append(({k: svv.to_u32(o[k]) for k in snaps},) + tuple(ctx.bounds()[:2]))
+        want = solves.result()
+        for i, (q, (rows, cap, cup)) in enumerate(zip(qs, got)):
+            for k, row in rows.items():
+                np.testing.assert_array_equal(row, want[(("cap", q.win_begin + k, 1), q.type, q.source)],
+                                              err_msg=f"query {i} snapshot {q.win_begin + k}")
+            np.testing.assert_array_equal(cap, want[(("cap", q.win_begin, q.win_len), q.type, q.source)])
+            np.testing.assert_array_equal(cup, want[(("cup", q.win_begin, q.win_len), q.type, q.source)])
+        # Theorem 1 / 2 on every snapshot of every output (recomputed on the device)
+        for q in qs:
+            o = out[: q.win_len]
+            ctx.query(q.type, q.source, q.win_begin, q.win_len, out=o)
+            _check_invariants(o, want[(("cap", q.win_begin, q.win_len), q.type, q.source)],
+                              want[(("cup", q.win_begin, q.win_len), q.type, q.source)], q.type)
+    finally:
+        ctx.close()
+
+
+def test_rmat22_served_full(svv):
     log = W.rmat22(seed=1005, n_snapshots=128)
-    reqs = [q for _, q in W.serve_requests(log, 100, 0.3, seed=5)][:24]
+    reqs = [q for _, q in W.serve_requests(log, 100, 0.48, seed=5)]
+    deg = np.bincount(log.src.astype(np.int64), minlength=log.V)
+    full = _full_set(reqs, deg)
+    solves = OracleSolves(log)
+    _plan(solves, reqs, full)
+    solves.start()
     ctx = _load(svv, log)
     try:
         outs = [ctx.empty_out(q.win_len) for q in reqs]
         svv.svv_serve_start(ctx.h, max_window=100, capacity=64, arena_bytes=1 << 30)
-        tickets = [svv.svv_submit(ctx.h, q.type, q.source, q.win_begin, q.win_len, out=o) for q, o in zip(reqs, outs)]
+        tickets = [svv.svv_submit(ctx.h, q.type, q.source, q.win_begin, q.win_len, out=o)
+                   for q, o in zip(reqs, outs)]
         assert all(t is not None for t in tickets)
         for t in tickets:
             assert svv.svv_poll(ctx.h, t, wait=True) == 0
             svv.svv_release(ctx.h, t)
         svv.svv_serve_stop(ctx.h)
-        alone = ctx.empty_out(100)
+        bounds = []
         for q, o in zip(reqs, outs):
-            ctx.query(q.type, q.source, q.win_begin, q.win_len, out=alone[: q.win_len])
-            assert torch.equal(o, alone[: q.win_len])
-        _check_sampled(svv, log, ctx, reqs[0], outs[0])
+            assert torch.equal(o, ctx.query(q.type, q.source, q.win_begin, q.win_len))
+            bounds.append(ctx.bounds()[:2])
+        want = solves.result()
+        _verify(svv, ctx, log, reqs, outs, want, full)
+        for q, (cap, cup) in zip(reqs, bounds):
+            np.testing.assert_array_equal(cap, want[(("cap", q.win_begin, q.win_len), q.type, q.source)])
+            np.testing.assert_array_equal(cup, want[(("cup", q.win_begin, q.win_len), q.type, q.source)])
     finally:
         ctx.close()

@@ -1,4 +1,6 @@
-"""Autotuner: picks per-type knobs by timing a probe query; results stay exact."""
+"""Autotuner: picks per-type, per-window-length knobs by timing a probe query
+(pull threshold, near-far width, work-unit size, CTAs per SM, relaxation lanes,
+chunk skipping, slab width); results stay exact."""
 import numpy as np
 import pytest
 
@@ -20,6 +22,8 @@ def test_autotune_keeps_results_exact():
             r = svv.svv_autotune(ctx.h, t, 0, 0, log.S, reps=2)
             assert r["candidates"] >= 2
             assert r["solve_chunk"] in (32, 64) and r["relax_lanes"] in (16, 32)
+            assert r["pull_pct"] in (0, 5, 10, 15, 25, 40) and r["slab_max"] in (128, 64, 32)
+            assert r["delta"] in ((0, 250, 1000, 4000) if t == 0 else (0,))
             assert 0 < r["best_ms"] <= r["default_ms"]
             for b, L in [(0, log.S), (5, 9)]:
                 np.testing.assert_array_equal(svv.to_u32(ctx.query(t, 3, b, L)), oracle.query(log, t, 3, b, L))

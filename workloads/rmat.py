@@ -168,19 +168,28 @@ def make_log(
         n_total += n_add
         # deleted positions are refilled by the new instances (order of the
         # live list is arbitrary but deterministic); the surplus is appended
-        # or removed
+        # or swapped out
         m = min(n_add, n_del)
         live[pos[:m]] = new_ids[:m]
         if add_mode == "skewed":
             live_src[pos[:m]] = as_[:m]
             live_dst[pos[:m]] = ad[:m]
         if n_del > m:
-            rest = np.zeros(live.shape[0], dtype=bool)
-            rest[pos[m:]] = True
-            live = live[~rest]
+            # the surplus deleted positions take the last live instances
+            # (highest position first), so no step copies the whole list
+            n_live = live.shape[0]
+            for p in np.sort(pos[m:])[::-1].tolist():
+                last = n_live - 1
+                if p != last:
+                    live[p] = live[last]
+                    if add_mode == "skewed":
+                        live_src[p] = live_src[last]
+                        live_dst[p] = live_dst[last]
+                n_live -= 1
+            live = live[:n_live]
             if add_mode == "skewed":
-                live_src = live_src[~rest]
-                live_dst = live_dst[~rest]
+                live_src = live_src[:n_live]
+                live_dst = live_dst[:n_live]
         if n_add > m:
             live = np.concatenate([live, new_ids[m:]])
             if add_mode == "skewed":
