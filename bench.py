@@ -44,8 +44,8 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["svv", "reference"], default="svv")
-    p.add_argument("--workload", choices=["rmat20", "small", "batch22", "batch16", "rmat24", "serve22", "serve16",
-                                          "sensitivity", "ablation"],
+    p.add_argument("--workload", choices=["rmat20", "small", "batch22", "batch20", "batch16", "rmat24", "serve22",
+                                          "serve16", "sensitivity", "ablation"],
                    default="rmat20",
                    help="rmat20: the headline line; batch*: many mixed queries in one launch; rmat24: the "
                         "two-mask-word scale-24 graph; serve*: Poisson request streams")
@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
                    help="library tuning knob (svv_set_tuning), repeatable")
+    p.add_argument("--autotune", action="store_true",
+                   help="batch*/serve*: run svv_autotune per query type and window-length bucket before warm-up")
     p.add_argument("--verbose", action="store_true")
     return p.parse_args()
 
@@ -233,6 +235,28 @@ def _isolated(log, source):
     return bool(deg[source] == 0)
 
 
+def _len_bucket(L):
+    """Window-length bucket of the library's tuned knobs (up to 8, 16, 32, 64, more)."""
+    return 0 if L <= 8 else 1 if L <= 16 else 2 if L <= 32 else 3 if L <= 64 else 4
+
+
+def _autotune(svv, ctx, log, qs):
+    """svv_autotune on one probe query (the first with a source that has
+    out-edges) of every (type, window-length bucket) in qs; returns the knobs
+    it kept, keyed by type and bucket bound."""
+    probes = {}
+    for q in qs:
+        key = (q.type, _len_bucket(q.win_len))
+        if key not in probes and not _isolated(log, q.source):
+            probes[key] = q
+    bound = ["<=8", "<=16", "<=32", "<=64", ">64"]
+    out = {}
+    for (t, b), q in sorted(probes.items()):
+        r = svv.svv_autotune(ctx.h, t, q.source, q.win_begin, q.win_len, reps=2)
+        out[f"{W.TYPE_NAMES[t]}_L{bound[b]}"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+    return out
+
+
 def _batch_launches(log, qs, gmax):
     """Kernel launches of an in-order batch: a query whose source has no
     out-edge is one fill; the others run in groups of up to gmax of one type
@@ -355,6 +379,14 @@ def _tune(ctx, args):
         ctx.set_tuning(k, int(v))
 
 
+def _tuning(args, tuned=None):
+    """config.tuning: the --tune knobs, and what the autotuner kept."""
+    d = dict(kv.split("=", 1) for kv in args.tune)
+    if tuned is not None:
+        d["autotuned"] = tuned
+    return d
+
+
 def _clocks_start(rank, args, dev):
     s = ClockSampler(gpu_id_of(dev)) if (rank == 0 and not args.no_clocks) else None
     if s:
@@ -376,11 +408,17 @@ def run_batch(args, world, rank, local):
     if args.workload == "batch22":
         log, nq = W.rmat22(), 256
         desc = "RMAT scale 22 (V=4,194,304, E0=67,108,864) w[1,999] S=64, 0.05% churn/step; 256 mixed queries, L in [8,64]"
+    elif args.workload == "batch20":
+        log, nq = W.rmat20(), 16
+        desc = ("RMAT scale 20 (V=1,048,576, E0=16,777,216) w[1,999] S=64, 10k del + 10k RMAT add per step; "
+                "16 mixed queries, L in [8,64]")
+        args.tune = ["batch_mode=2"] + list(args.tune)  # query groups at this size too
     else:
         log, nq = W.scaled_rmat(16, 16, 64, 0.0005, 1016), 64
         desc = "RMAT scale 16 (V=65,536, E0=1,048,576) w[1,999] S=64, 0.05% churn/step; 64 mixed queries, L in [8,64]"
     qs = W.batch_queries(log, n=nq, seed=3)
     ctx = _setup_ctx(svv, log, dev, args)
+    tuned = _autotune(svv, ctx, log, qs) if args.autotune else None
     outs = [ctx.empty_out(q.win_len) for q in qs]
     specs = [(q.type, q.source, q.win_begin, q.win_len, o) for q, o in zip(qs, outs)]
     stream = torch.cuda.current_stream(dev)
@@ -430,7 +468,7 @@ def run_batch(args, world, rank, local):
             "config": {"workload": desc, "queries": nq, "output_bytes": int(vals * 4),
                        "mode": "one launch" if one_launch else "in order",
                        "teams": stats["batch_teams"], "team_blocks": stats["batch_team_blocks"],
-                       "tuning": dict(kv.split("=", 1) for kv in args.tune)},
+                       "tuning": _tuning(args, tuned)},
             "one_at_a_time": {"value": vals / (seq_ms / 1e3), "unit": UNIT, "ms": seq_ms},
             "plain_sample": {"value": plain_value, "unit": UNIT, "queries": len(sample), "ms": plain_ms},
             "clocks": clocks,
@@ -496,7 +534,8 @@ def run_serve(args, world, rank, local):
     """Poisson request streams at 100, 1,000 and 10,000 requests/s (type
     uniform, source uniform, L uniform in [8, 100] at a uniform offset) served
     with arena admission -- by the live batch kernel below 2M vertices, in
-    order (each request as svv_query's kernels) from 2M; the plain
+    query groups from 2M (up to 8 same-type requests share the bound solves,
+    then each runs its own extraction, relaxation and scatter); the plain
     per-snapshot recompute served FIFO on the first requests of the 100/s
     stream."""
     import torch
@@ -513,10 +552,13 @@ def run_serve(args, world, rank, local):
         log = W.scaled_rmat(16, 16, 128, 0.0005, 1016)
         desc = "RMAT scale 16 (V=65,536, E0=1,048,576) w[1,999] S=128, 0.05% churn/step"
     ctx = _setup_ctx(svv, log, dev, args)
+    tuned = _autotune(svv, ctx, log, [q for _, q in W.serve_requests(log, 1000, 1.0, seed=5)]) if args.autotune else None
     arena = (64 << 30) if args.workload == "serve22" else (2 << 30)
     svv.svv_serve_start(ctx.h, max_window=min(100, log.S), capacity=1 << 16, arena_bytes=arena)
     bm = int(dict(kv.split("=", 1) for kv in args.tune).get("batch_mode", 0))
-    mode = "in order" if bm == 2 or (bm == 0 and log.V >= (2 << 20)) else "live kernel"
+    gm = int(dict(kv.split("=", 1) for kv in args.tune).get("group_max", 8))
+    mode = (("query groups of up to %d" % gm if gm > 1 else "in order")
+            if bm == 2 or (bm == 0 and log.V >= (2 << 20)) else "live kernel")
     dur = args.serve_seconds
     warm = 1.0
     results = {}
@@ -560,7 +602,7 @@ def run_serve(args, world, rank, local):
             "config": {"workload": desc + f"; Poisson 100/1,000/10,000 req/s, each stream min({dur:g} s, 2,500 requests), "
                                    "first 10% excluded",
                        "arena_bytes": arena, "admission": "output arena (svv_submit refuses when full)",
-                       "mode": mode},
+                       "mode": mode, "tuning": _tuning(args, tuned)},
             "serve": results, "plain_fifo": plain}), flush=True)
     ctx.close()
     return 0
@@ -698,7 +740,7 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
-    if args.workload in ("batch22", "batch16"):
+    if args.workload in ("batch22", "batch20", "batch16"):
         return run_batch(args, world, rank, local)
     if args.workload == "rmat24":
         return run_rmat24(args, world, rank, local)
