@@ -56,6 +56,10 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
                    help="library tuning knob (svv_set_tuning), repeatable")
+    p.add_argument("--batch-queries", type=int, default=0,
+                   help="batch*: number of queries (default: the workload's own)")
+    p.add_argument("--batch-max-len", type=int, default=0,
+                   help="batch*: cap every window at this many snapshots (a small case of the same mix)")
     p.add_argument("--autotune", action="store_true",
                    help="batch*/serve*: run svv_autotune per query type and window-length bucket before warm-up")
     p.add_argument("--verbose", action="store_true")
@@ -416,7 +420,13 @@ def run_batch(args, world, rank, local):
     else:
         log, nq = W.scaled_rmat(16, 16, 64, 0.0005, 1016), 64
         desc = "RMAT scale 16 (V=65,536, E0=1,048,576) w[1,999] S=64, 0.05% churn/step; 64 mixed queries, L in [8,64]"
+    if args.batch_queries:
+        nq = args.batch_queries
+        desc += f"; this run: {nq} queries of the same mix"
     qs = W.batch_queries(log, n=nq, seed=3)
+    if args.batch_max_len:
+        qs = [W.Query(q.type, q.source, q.win_begin, min(q.win_len, args.batch_max_len)) for q in qs]
+        desc += f"; windows capped at {args.batch_max_len} snapshots"
     ctx = _setup_ctx(svv, log, dev, args)
     tuned = _autotune(svv, ctx, log, qs) if args.autotune else None
     outs = [ctx.empty_out(q.win_len) for q in qs]

@@ -196,8 +196,9 @@ __device__ bool group_solve_team(const GroupArgs& a, const Team& t, unsigned lon
       const uint32_t EF = g.E - g.NF;
       const uint32_t ntot = EF + g.NF;
       const uint32_t nchunks = (ntot + 63u) >> 6;
-      for (uint32_t ch = gwarp; ch < nchunks; ch += nwarps) {
-        uint32_t d[2], src[2], w[2], pm[2];
+      // the next chunk's edges are loaded while this chunk's rows are gathered
+      auto load_chunk = [&](uint32_t ch, bool valid, uint32_t (&d)[2], uint32_t (&src)[2], uint32_t (&w)[2],
+                            uint32_t (&pm)[2]) {
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const uint32_t idx = (ch << 6) + 32u * j + lane;
@@ -205,23 +206,30 @@ __device__ bool group_solve_team(const GroupArgs& a, const Team& t, unsigned lon
           src[j] = 0;
           w[j] = 0;
           pm[j] = 0;
-          if (idx < ntot) {
+          if (valid && idx < ntot) {
             if (idx < EF) {
-              d[j] = __ldg(g.ifd + idx);
-              const uint2 sw = __ldg(g.ifcw + idx);
+              d[j] = ld_stream(g.ifd + idx);
+              const uint2 sw = ld_stream(g.ifcw + idx);
               src[j] = sw.x;
               w[j] = sw.y;
               pm[j] = allmask;
             } else {
               const uint32_t k = idx - EF;
-              d[j] = __ldg(g.ipd + k);
-              const uint2 sw = __ldg(g.ipcw + k);
+              d[j] = ld_stream(g.ipd + k);
+              const uint2 sw = ld_stream(g.ipcw + k);
               src[j] = sw.x;
               w[j] = sw.y;
-              pm[j] = lanes_of<PRED>(__ldg(a.iplanes + k)) & allmask;
+              pm[j] = lanes_of<PRED>(ld_stream(a.iplanes + k)) & allmask;
             }
           }
         }
+      };
+      uint32_t d[2], src[2], w[2], pm[2];
+      load_chunk(gwarp, gwarp < nchunks, d, src, w, pm);
+      for (uint32_t ch = gwarp; ch < nchunks; ch += nwarps) {
+        uint32_t dn[2], srcn[2], wn[2], pmn[2];
+        const bool more = ch + nwarps < nchunks;
+        load_chunk(more ? ch + nwarps : ch, more, dn, srcn, wn, pmn);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const uint32_t idx = (ch << 6) + 32u * j + lane;
@@ -270,6 +278,13 @@ __device__ bool group_solve_team(const GroupArgs& a, const Team& t, unsigned lon
               ++changed;
             }
           }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          d[j] = dn[j];
+          src[j] = srcn[j];
+          w[j] = wn[j];
+          pm[j] = pmn[j];
         }
       }
       if (lane == 0) relaxed += scanned;
