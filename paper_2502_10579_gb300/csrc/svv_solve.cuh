@@ -171,7 +171,18 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
             }
           }
         }
-        uint32_t cand[4];
+        // the lowest lane of each target's run loads the target's value now,
+        // alongside the source gathers, instead of after the fold
+        uint32_t cand[4], tv[4];
+        unsigned lead = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const unsigned grp = __match_any_sync(kFullMask, d[j]);
+          const uint32_t idx = (ch << 7) + 32u * j + lane;
+          const bool ld = idx < ntot && lane == (unsigned)(__ffs(grp) - 1);
+          lead |= (ld ? 1u : 0u) << j;
+          tv[j] = ld ? ld_val(a.val + d[j]) : 0u;
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           cand[j] = Op::kIdentity;
@@ -186,8 +197,7 @@ __device__ bool solve_team(const SolveArgs& a, const Team& t, unsigned long long
           const unsigned grp = __match_any_sync(kFullMask, d[j]);
           const uint32_t best =
               Op::better(0u, 1u) ? __reduce_min_sync(grp, cand[j]) : __reduce_max_sync(grp, cand[j]);
-          const uint32_t idx = (ch << 7) + 32u * j + lane;
-          if (idx < ntot && lane == (unsigned)(__ffs(grp) - 1) && Op::better(best, ld_val(a.val + d[j]))) {
+          if (((lead >> j) & 1u) && Op::better(best, tv[j])) {
             Op::red(a.val + d[j], best);
             // a plain store: the next round finds the changed vertices from
             // the stamps, so `changed` only needs to be zero exactly when
