@@ -51,6 +51,9 @@ def parse():
                         "two-mask-word scale-24 graph; serve*: Poisson request streams")
     p.add_argument("--serve-seconds", type=float, default=10.0)
     p.add_argument("--plain-steps", type=int, default=1, help="timed steps of the plain recompute (0 = skip)")
+    p.add_argument("--step-api", choices=["groups", "async"], default="groups",
+                   help="rmat20/small: the step's queries in one svv_query_batch call as one query group of "
+                        "mixed types (groups), or one svv_query_async call per query (async)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
@@ -197,6 +200,17 @@ def layout_bytes(phase, gc, st, L):
     return 0
 
 
+def group_layout_bytes(phase, gc, n):
+    """The floor of one group solve of n queries: the graph once, n values
+    per vertex."""
+    V, E, NF, Wd = gc["V"], gc["E"], gc["NF"], gc["W"]
+    if phase == "cap":
+        return 8 * (V + 1) + 8 * (E - NF) + 4 * n * V
+    if phase == "cup":
+        return NF * (4 + 8 + 8 * Wd) + 8 * (V + 1) + 8 * E + 8 * NF * Wd + 8 * n * V
+    return 0
+
+
 PHASE_KERNELS = {"cap": "solve_kernel<Op, kPredAll> (intersection graph)",
                  "cup": "solve_kernel<Op, kPredAny> (union graph)",
                  "qrs": "qrs_kernel (stable compaction + subgraph)",
@@ -204,8 +218,17 @@ PHASE_KERNELS = {"cap": "solve_kernel<Op, kPredAll> (intersection graph)",
                  "scatter": "scatter_kernel (output)"}
 
 
-KERNEL_SOURCES = {"cap": ["svv_solve.cu", "svv_solve.cuh", "svv_team.cuh", "svv_device.cuh", "svv_push.cuh",
-                          "svv_internal.h"]}
+GROUP_KERNELS = {"cap": "group_solve_kernel<OpMixed, KL, kPredAll> (intersection graphs of the step's queries, "
+                        "one launch)",
+                 "cup": "group_solve_kernel<OpMixed, KL, kPredAny> (union graphs of the step's queries, one launch)"}
+
+# kernel -> (profile summary holding its traffic line, sources whose hash it names)
+KERNEL_SOURCES = {"cap": ("solve_kernel_rmat20.md",
+                          ["svv_solve.cu", "svv_solve.cuh", "svv_team.cuh", "svv_device.cuh", "svv_push.cuh",
+                           "svv_internal.h"]),
+                  "group_cap": ("group_solve_kernel_rmat20_pair.md",
+                                ["svv_group.cu", "svv_group.cuh", "svv_team.cuh", "svv_device.cuh", "svv_push.cuh",
+                                 "svv_internal.h"])}
 
 
 def recorded_traffic(kernel, workload):
@@ -215,12 +238,13 @@ def recorded_traffic(kernel, workload):
     import re
     if workload != "rmat20" or kernel not in KERNEL_SOURCES:
         return None
+    prof, srcs = KERNEL_SOURCES[kernel]
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES[kernel]:
+    for f in srcs:
         with open(os.path.join(ROOT, "paper_2502_10579_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     try:
-        with open(os.path.join(ROOT, "profiles", "solve_kernel_rmat20.md")) as fh:
+        with open(os.path.join(ROOT, "profiles", prof)) as fh:
             for line in fh:
                 m = re.match(r"traffic: kernel=(\w+) bytes_per_launch=(\d+) sources_sha256=(\w+)", line.strip())
                 if m and m.group(1) == kernel and m.group(3) == h.hexdigest():
@@ -783,6 +807,18 @@ def main():
     outs = [ctx.empty_out(q.win_len) for q in qs]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=f"cuda:{dev}")
     stream = torch.cuda.current_stream(dev)
+    groups = args.step_api == "groups"
+    if groups:  # the step's queries share one query group whatever their types
+        ctx.set_tuning("batch_mode", 2)
+        ctx.set_tuning("group_mix", 1)
+    specs = [(q.type, q.source, q.win_begin, q.win_len, o) for q, o in zip(qs, outs)]
+
+    def step_groups():
+        """One step: the step's queries in one svv_query_batch call (one query
+        group of mixed types), which returns after the step."""
+        st = svv.svv_query_batch(ctx.h, specs, stream)
+        if any(st):
+            raise RuntimeError(f"batched step failed: {st}")
 
     def step_async():
         """One step: every query queued on the stream (svv_query_async), no host wait."""
@@ -797,8 +833,11 @@ def main():
         return sts
 
     for _ in range(args.warmup):
-        for tk in step_async():
-            svv.svv_query_wait(ctx.h, tk)
+        if groups:
+            step_groups()
+        else:
+            for tk in step_async():
+                svv.svv_query_wait(ctx.h, tk)
         flush.zero_()
     torch.cuda.synchronize()
 
@@ -813,7 +852,10 @@ def main():
     pygc.disable()  # keep collector pauses out of the timed steps
     for i in range(args.steps):
         starts[i].record(stream)
-        tickets += step_async()
+        if groups:
+            step_groups()
+        else:
+            tickets += step_async()
         ends[i].record(stream)
         flush.zero_()  # L2 flush between timed steps, outside the event pair
         if len(tickets) > 32:  # the library keeps 64 queries in flight
@@ -845,6 +887,16 @@ def main():
                 phase_ms[k] += st["ms_" + k]
         all_stats.append(sts)
     torch.cuda.synchronize()
+    # the group solves of the batched step, timed by the library
+    group_ms = {"cap": 0.0, "cup": 0.0}
+    if groups:
+        for _ in range(nphase):
+            step_groups()
+            gst = ctx.stats()
+            group_ms["cap"] += gst["ms_group_cap"]
+            group_ms["cup"] += gst["ms_group_cup"]
+            flush.zero_()
+        torch.cuda.synchronize()
     ctx.set_tuning("phase_timing", 0)
 
     # plain per-snapshot recompute on the same queries
@@ -874,6 +926,11 @@ def main():
     # next query computes); the same through svv_query_host one at a time
     e2e = None
     if not args.no_e2e:
+        # results into host memory: the host link, not the kernels, bounds the
+        # step, and queries run one after another start the first result's copy
+        # earlier than a shared group does (measured), so no type mixing here
+        if groups:
+            ctx.set_tuning("group_mix", 0)
         hosts = [torch.empty((q.win_len, log.V), dtype=torch.int32, pin_memory=True) for q in qs]
         hspecs = [(q.type, q.source, q.win_begin, q.win_len, h) for q, h in zip(qs, hosts)]
         assert svv.svv_query_batch(ctx.h, hspecs) == [0] * len(qs)
@@ -893,7 +950,8 @@ def main():
                "h2d_bytes_per_step": len(qs) * ctypes.sizeof(svv.svv_query_spec),
                "d2h_bytes_per_step": int(sum(q.win_len * log.V * 4 for q in qs)),
                "inputs": "the step's query arguments (svv_query_spec); the graph stays resident on the device",
-               "api": "svv_query_batch, pinned host outputs",
+               "api": "svv_query_batch, pinned host outputs, one query after another (each result copied "
+                      "back while the next computes)",
                "one_at_a_time": {"value": values_per_step * args.steps * world / dt1, "api": "svv_query_host"}}
 
     if rank == 0:
@@ -909,36 +967,56 @@ def main():
         # table's per-unit figures, and separately the resident layout's
         # floor) over the phase's average event-timed duration
         nlaunch = nphase * len(qs)
+        grouped = [q for q in qs if not _isolated(log, q.source)]
         phases = []
         for ph in ("cap", "cup", "qrs", "relax", "scatter"):
-            ms = phase_ms[ph] / nlaunch
-            sb = sum(survey_bytes(ph, gc, st, q.win_len) for sts in all_stats for st, q in zip(sts, qs)) / nlaunch
-            lb = sum(layout_bytes(ph, gc, st, q.win_len) for sts in all_stats for st, q in zip(sts, qs)) / nlaunch
+            if groups and ph in ("cap", "cup") and len(grouped) > 1:
+                # one group launch solves every query of the step: its
+                # algorithmic bytes are the member queries' (one unit each),
+                # its floor reads the graph once for all of them
+                ms = group_ms[ph] / nphase
+                sb = sum(survey_bytes(ph, gc, None, q.win_len) for q in grouped)
+                lb = group_layout_bytes(ph, gc, len(grouped))
+                kname, tkey = GROUP_KERNELS[ph], "group_" + ph
+            else:
+                ms = phase_ms[ph] / nlaunch
+                sb = sum(survey_bytes(ph, gc, st, q.win_len) for sts in all_stats for st, q in zip(sts, qs)) / nlaunch
+                lb = sum(layout_bytes(ph, gc, st, q.win_len) for sts in all_stats for st, q in zip(sts, qs)) / nlaunch
+                kname, tkey = PHASE_KERNELS[ph], ph
             a = sb / (ms / 1e3) / 1e9 if ms > 0 else 0.0
             al = lb / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-            phases.append({"phase": ph, "kernel": PHASE_KERNELS[ph], "avg_launch_ms": ms,
+            phases.append({"phase": ph, "kernel": kname, "avg_launch_ms": ms, "traffic_key": tkey,
                            "algorithmic_bytes_per_launch": sb, "achieved": a, "frac": a / hbm_peak,
                            "layout_floor": {"bytes_per_launch": lb, "achieved": al, "frac": al / hbm_peak}})
         dom = max(phases, key=lambda p: p["avg_launch_ms"])
+        if groups and len(grouped) > 1:
+            ph_step = {k: (group_ms[k] / nphase if k in group_ms else v / nphase) for k, v in phase_ms.items()}
+            launches = len(qs) - len(grouped) + 4 + 3 * len(grouped)
+            api = ("svv_query_batch: the step's queries in one call, one query group of mixed types "
+                   "(batch_mode 2, group_mix 1); the call returns after the step")
+        else:
+            ph_step = {k: v / nphase for k, v in phase_ms.items()}
+            launches = sum(1 if _isolated(log, q.source) else 5 for q in qs)
+            api = "svv_query_async per query, one stream, no host wait inside a step"
         last = all_stats[-1]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": desc, "queries_per_step": len(qs), "l2": "flushed between steps (512 MB write)",
-                       "api": "svv_query_async per query, one stream, no host wait inside a step",
+                       "api": api,
                        "parallelism": f"replicas x{world}", "tuning": dict(kv.split("=", 1) for kv in args.tune)},
             "roofline": {"bound": "hbm", "kernel": dom["kernel"], "phase": dom["phase"],
                          "achieved": dom["achieved"], "peak": hbm_peak,
                          "peak_source": peak_src + " (copy bandwidth, burst)", "unit": "GB/s", "frac": dom["frac"],
                          "algorithmic_bytes_per_launch": dom["algorithmic_bytes_per_launch"],
                          "avg_launch_ms": dom["avg_launch_ms"],
-                         "traffic": recorded_traffic(dom["phase"], args.workload),
+                         "traffic": recorded_traffic(dom["traffic_key"], args.workload),
                          "layout_floor": dom["layout_floor"]},
             "roofline_phases": phases,
-            "phase_ms_per_step": {k: v / nphase for k, v in phase_ms.items()},
+            "phase_ms_per_step": ph_step,
             "plain": plain, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": args.steps * sum(1 if _isolated(log, q.source) else 5 for q in qs),
+            "gpu_launches": args.steps * launches,
             "query_stats": [{k: v for k, v in st.items() if not k.startswith("ms_")} for st in last],
         }
         if not args.no_cpu_baseline and world == 1:  # timed on the host at N=1 only

@@ -91,6 +91,10 @@ typedef struct {
     float ms_batch;           /* device span of the last svv_query_batch (first start to last end) */
     uint32_t batch_teams;     /* teams the last batch ran with */
     uint32_t batch_team_blocks;
+    /* device time of the last query group's intersection-graph and union-graph
+     * solves in the last in-order svv_query_batch, when "phase_timing" is 1
+     * (and "graph" is 0); 0 otherwise */
+    float ms_group_cap, ms_group_cup;
 } svv_stats;
 
 /* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the bytes
@@ -167,7 +171,8 @@ svv_status svv_query_wait(svv_ctx *ctx, uint64_t ticket, int wait);
  * pipeline of svv_query for each, with its own scratch, so instances overlap
  * on the GPU.  From 2M vertices, where one query's rounds already fill the
  * GPU, the instances run in QUERY GROUPS: up to "group_max" (default 8)
- * instances of one type, in arrival order, share one intersection-graph solve
+ * instances of one type (of any types with "group_mix"), in arrival order,
+ * share one intersection-graph solve
  * and one union-graph solve -- one set of frontier rounds in which every
  * vertex holds one value per member query (a query-oblivious frontier, as
  * Section 4.2 shares one frontier between snapshots), so each round reads
@@ -386,7 +391,11 @@ svv_status svv_autotune(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t w
  * timing is not recorded in this mode; an in-order svv_query_batch with
  * device outputs likewise captures all its launches into one graph),
  * "group_max" (1..8, default 8: queries per group of an in-order batch and of
- * the server from 2M vertices; 1 runs every query alone), "group_pull_pct" /
+ * the server from 2M vertices; 1 runs every query alone), "group_mix" (0
+ * default: a group holds queries of one type; 1: queries of any types share a
+ * group, every lane solved in the min lattice with its own relaxation --
+ * SSWP lanes on complemented widths, converted back when the bounds are
+ * split -- results identical), "group_pull_pct" /
  * "group_pull_pct_union" (0..100, defaults 15 / 100: a group's intersection /
  * union solve pulls when its frontier holds more than this % of all work
  * units; 0 or 100 = push only), "isolated_fast" (1 default: a query whose

@@ -200,8 +200,10 @@ svv_status svv_create(svv_ctx** out, int device, uint64_t budget) {
   c->occ_qrs = occupancy_qrs(c->threads);
   c->occ_relax = occupancy_relax(c->threads);
   c->occ_batch = occupancy_batch(c->threads);
-  c->occ_group = occupancy_group(c->threads);
-  if (c->occ_solve <= 0 || c->occ_qrs <= 0 || c->occ_relax <= 0 || c->occ_batch <= 0 || c->occ_group <= 0) {
+  c->occ_group = occupancy_group(c->threads, false);
+  c->occ_group2 = occupancy_group(c->threads, true);
+  if (c->occ_solve <= 0 || c->occ_qrs <= 0 || c->occ_relax <= 0 || c->occ_batch <= 0 || c->occ_group <= 0 ||
+      c->occ_group2 <= 0) {
     delete c;
     return SVV_ECUDA;
   }
@@ -228,6 +230,8 @@ void svv_destroy(svv_ctx* c) {
     for (auto& e : c->ev)
       if (e) cudaEventDestroy(e);
     for (auto& e : c->bev)
+      if (e) cudaEventDestroy(e);
+    for (auto& e : c->gev)
       if (e) cudaEventDestroy(e);
     for (int i = 0; i < 2; ++i) {
       if (c->ev_done[i]) cudaEventDestroy(c->ev_done[i]);
@@ -300,6 +304,9 @@ svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
   } else if (k == "batch_mode") {
     if (v < 0 || v > 2) return fail(c, SVV_EINVAL, "batch_mode is 0 (by graph size), 1 (one launch) or 2 (in order)");
     c->batch_mode = (int)v;
+  } else if (k == "group_mix") {
+    if (v < 0 || v > 1) return fail(c, SVV_EINVAL, "group_mix: 0 or 1");
+    c->group_mix = v != 0;
   } else if (k == "group_pull_pct" || k == "group_pull_pct_union") {
     if (v < 0 || v > 100) return fail(c, SVV_EINVAL, k + " in [0, 100]");
     c->group_pull_pct[k == "group_pull_pct" ? 0 : 1] = (uint32_t)v;
@@ -897,7 +904,8 @@ std::vector<std::vector<uint32_t>> form_groups(const svv_ctx* c, const BatchInst
       groups.push_back({k});
       continue;
     }
-    const int t = std::max(0, std::min(3, inst[k].type));
+    // with group_mix every type shares one group stream
+    const int t = c->group_mix ? 0 : std::max(0, std::min(3, inst[k].type));
     if (open[t] < 0 || groups[open[t]].size() >= std::max<uint32_t>(1, gmax)) {
       open[t] = (int)groups.size();
       groups.emplace_back();

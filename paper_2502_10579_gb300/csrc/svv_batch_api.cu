@@ -251,6 +251,12 @@ extern "C" svv_status svv_query_batch(svv_ctx* c, uint32_t n, svv_query_spec* sp
     c->stats = svv_stats{};
     c->stats.ms_batch = ms;
     c->stats.batch_teams = 0;
+    if (c->gev_pending) {  // the stream was synchronised at the end of the batch
+      cudaEventElapsedTime(&c->stats.ms_group_cap, c->gev[0], c->gev[1]);
+      cudaEventElapsedTime(&c->stats.ms_group_cup, c->gev[1], c->gev[2]);
+      c->stats.phase_timing = 1;
+      c->gev_pending = false;
+    }
     if (overall) return fail(c, overall, "some batched queries failed");
     c->err.clear();
     return SVV_OK;

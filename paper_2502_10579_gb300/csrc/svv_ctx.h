@@ -212,6 +212,8 @@ struct svv_ctx {
   int batch_mode = 0;   // 0: by graph size, 1: one launch, 2: in order
   int occ_batch = 0;
   cudaEvent_t bev[2] = {};  // span of an in-order batch
+  cudaEvent_t gev[3] = {};  // phase timing of the last query group: before, between and after its solves
+  bool gev_pending = false;
 
   // query groups: lane rows of the two bounds, per-lane planar copies, lane
   // words of the partial edges, the group's error word
@@ -219,7 +221,9 @@ struct svv_ctx {
   // pull threshold of the group solves (intersection, union), % of all units:
   // a group pull round gathers a whole lane row per in-edge, so groups pull later
   uint32_t group_pull_pct[2] = {15, 100};
-  int occ_group = 0;
+  bool group_mix = false;  // groups may hold queries of different types
+  int occ_group = 0;   // group solves of 4 or 8 lanes
+  int occ_group2 = 0;  // of 2 lanes
   bool group_ready = false;
   std::vector<void*> group_bufs;
   uint32_t *gcap = nullptr, *gcup = nullptr, *gnfl = nullptr, *gipl = nullptr, *gerr = nullptr;

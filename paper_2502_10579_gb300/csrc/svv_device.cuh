@@ -263,6 +263,46 @@ struct OpSSNP {  // CASMIN(Val(v), max(Val(u), w))
   __device__ __forceinline__ static void red(uint32_t* p, uint32_t v) { atomicMin(p, v); }  // no return: a reduction
 };
 
+// A query group may mix types.  Every type's values then live in the min
+// lattice (identity kInf, source 0): SSSP, BFS and SSNP already do, and SSWP's
+// widths are kept as complements, since the widest path (max over paths of
+// the min weight) is the complement of the min over paths of the max
+// complemented weight.  Each lane relaxes with its own kind (kKind*).
+
+struct OpMixed {
+  static constexpr bool kLevels = false;
+  static constexpr uint32_t kIdentity = kInf;
+  static constexpr uint32_t kSource = 0;
+  __device__ __forceinline__ static uint32_t relax_kind(uint32_t kind, uint32_t sv, uint32_t w) {
+    if (sv == kInf) return kInf;
+    if (kind == kKindSum) {
+      const unsigned long long s = (unsigned long long)sv + w;
+      return s > kSat ? kSat : (uint32_t)s;
+    }
+    if (kind == kKindHop) return sv + 1u;
+    const uint32_t x = kind == kKindMax ? w : ~w;
+    return sv > x ? sv : x;
+  }
+  __device__ __forceinline__ static bool better(uint32_t a, uint32_t b) { return a < b; }
+  __device__ __forceinline__ static void red(uint32_t* p, uint32_t v) { atomicMin(p, v); }
+};
+
+template <class Op>
+struct is_mixed {
+  static constexpr bool value = false;
+};
+template <>
+struct is_mixed<OpMixed> {
+  static constexpr bool value = true;
+};
+
+// lane k's relaxation: the op's own, or lane k's kind (2 bits of `kinds`)
+template <class Op>
+__device__ __forceinline__ uint32_t lane_relax(uint32_t kinds, int k, uint32_t sv, uint32_t w) {
+  if constexpr (is_mixed<Op>::value) return OpMixed::relax_kind((kinds >> (2 * k)) & 3u, sv, w);
+  else return Op::relax(sv, w);
+}
+
 // ---------------------------------------------------------------------------
 // Window predicates on a W-word presence mask (bit i = snapshot i).
 __device__ __forceinline__ uint64_t window_word(Window w, uint32_t j) {

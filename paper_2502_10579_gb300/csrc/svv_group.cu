@@ -9,6 +9,8 @@
 //     where the per-query phases (stable compaction, subgraph extraction,
 //     relaxation, scatter) read them.
 #include <algorithm>
+#include <iterator>
+#include <vector>
 
 #include "svv_group.cuh"
 
@@ -43,8 +45,9 @@ __global__ void __launch_bounds__(256) group_lanes_kernel(LanesArgs a) {
   }
 }
 
+// two-lane groups fit 40 registers: 3 CTAs per SM, as the single solve
 template <class Op, int KL, int PRED>
-__global__ void __launch_bounds__(kGroupThreads, 2) group_solve_kernel(GroupArgs a) {
+__global__ void __launch_bounds__(kGroupThreads, KL == 2 ? 3 : 2) group_solve_kernel(GroupArgs a) {
   __shared__ unsigned long long s_stage[(kGroupThreads / 32) * kStageUnits];
   const Team t{a.ctl, a.qerr, gridDim.x, blockIdx.x, a.spin_ns};
   group_solve_team<Op, KL, PRED>(a, t, s_stage);
@@ -56,19 +59,28 @@ template <int KL>
 __global__ void __launch_bounds__(256) group_split_kernel(SplitArgs a) {
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.V; v += gridDim.x * blockDim.x) {
     uint32_t ci[KL], cu[KL];
-    const uint4* pi = reinterpret_cast<const uint4*>(a.cap + (size_t)v * KL);
-    const uint4* pu = reinterpret_cast<const uint4*>(a.cup + (size_t)v * KL);
+    if constexpr (KL == 2) {
+      const uint2 x = __ldcs(reinterpret_cast<const uint2*>(a.cap + (size_t)v * KL));
+      const uint2 y = __ldcs(reinterpret_cast<const uint2*>(a.cup + (size_t)v * KL));
+      ci[0] = x.x, ci[1] = x.y;
+      cu[0] = y.x, cu[1] = y.y;
+    } else {
+      const uint4* pi = reinterpret_cast<const uint4*>(a.cap + (size_t)v * KL);
+      const uint4* pu = reinterpret_cast<const uint4*>(a.cup + (size_t)v * KL);
 #pragma unroll
-    for (int i = 0; i < KL / 4; ++i) {
-      const uint4 x = __ldcs(pi + i), y = __ldcs(pu + i);
-      ci[4 * i] = x.x, ci[4 * i + 1] = x.y, ci[4 * i + 2] = x.z, ci[4 * i + 3] = x.w;
-      cu[4 * i] = y.x, cu[4 * i + 1] = y.y, cu[4 * i + 2] = y.z, cu[4 * i + 3] = y.w;
+      for (int i = 0; i < KL / 4; ++i) {
+        const uint4 x = __ldcs(pi + i), y = __ldcs(pu + i);
+        ci[4 * i] = x.x, ci[4 * i + 1] = x.y, ci[4 * i + 2] = x.z, ci[4 * i + 3] = x.w;
+        cu[4 * i] = y.x, cu[4 * i + 1] = y.y, cu[4 * i + 2] = y.z, cu[4 * i + 3] = y.w;
+      }
     }
 #pragma unroll
     for (int k = 0; k < KL; ++k) {
       if ((uint32_t)k < a.nlanes) {
-        a.rI[k][v] = ci[k];
-        a.rU[k][v] = cu[k];
+        // a complemented lane (SSWP in a mixed group) gets its widths back
+        const uint32_t f = ((a.flip >> k) & 1u) ? 0xFFFFFFFFu : 0u;
+        a.rI[k][v] = ci[k] ^ f;
+        a.rU[k][v] = cu[k] ^ f;
       }
     }
   }
@@ -91,6 +103,7 @@ static cudaError_t launch_g(const GroupArgs& a, LaunchCfg cfg, cudaStream_t s) {
 
 template <class Op>
 static cudaError_t launch_gk(uint32_t KL, int pred, const GroupArgs& a, LaunchCfg cfg, cudaStream_t s) {
+  if (KL == 2) return pred == kPredAll ? launch_g<Op, 2, kPredAll>(a, cfg, s) : launch_g<Op, 2, kPredAny>(a, cfg, s);
   if (KL == 4) return pred == kPredAll ? launch_g<Op, 4, kPredAll>(a, cfg, s) : launch_g<Op, 4, kPredAny>(a, cfg, s);
   if (KL == 8) return pred == kPredAll ? launch_g<Op, 8, kPredAll>(a, cfg, s) : launch_g<Op, 8, kPredAny>(a, cfg, s);
   return cudaErrorInvalidValue;
@@ -101,22 +114,28 @@ cudaError_t launch_group_solve(int type, uint32_t KL, int pred, const GroupArgs&
     case 0: return launch_gk<OpSSSP>(KL, pred, a, cfg, s);
     case 1: return launch_gk<OpSSWP>(KL, pred, a, cfg, s);
     case 3: return launch_gk<OpSSNP>(KL, pred, a, cfg, s);
+    case kTypeMixed: return launch_gk<OpMixed>(KL, pred, a, cfg, s);
     default: return launch_gk<OpBFS>(KL, pred, a, cfg, s);
   }
 }
 
 cudaError_t launch_group_split(const SplitArgs& a, cudaStream_t s) {
   const uint32_t blocks = std::min<uint32_t>((a.V + 255u) / 256u, 152u * 16u);
-  if (a.KL == 4) group_split_kernel<4><<<blocks, 256, 0, s>>>(a);
+  if (a.KL == 2) group_split_kernel<2><<<blocks, 256, 0, s>>>(a);
+  else if (a.KL == 4) group_split_kernel<4><<<blocks, 256, 0, s>>>(a);
   else if (a.KL == 8) group_split_kernel<8><<<blocks, 256, 0, s>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 template <class Op>
-static int occ_g(int threads) {
-  const void* ks[] = {(const void*)group_solve_kernel<Op, 4, kPredAll>, (const void*)group_solve_kernel<Op, 4, kPredAny>,
-                      (const void*)group_solve_kernel<Op, 8, kPredAll>, (const void*)group_solve_kernel<Op, 8, kPredAny>};
+static int occ_g(int threads, bool two) {
+  const void* k2[] = {(const void*)group_solve_kernel<Op, 2, kPredAll>, (const void*)group_solve_kernel<Op, 2, kPredAny>};
+  const void* k48[] = {(const void*)group_solve_kernel<Op, 4, kPredAll>, (const void*)group_solve_kernel<Op, 4, kPredAny>,
+                       (const void*)group_solve_kernel<Op, 8, kPredAll>, (const void*)group_solve_kernel<Op, 8, kPredAny>};
+  std::vector<const void*> ks;
+  if (two) ks.assign(std::begin(k2), std::end(k2));
+  else ks.assign(std::begin(k48), std::end(k48));
   int best = 1 << 30;
   for (const void* k : ks) {
     int n = 0;
@@ -126,10 +145,12 @@ static int occ_g(int threads) {
   return best;
 }
 
-int occupancy_group(int threads) {
-  const int a = occ_g<OpSSSP>(threads), b = occ_g<OpSSWP>(threads), c = occ_g<OpBFS>(threads),
-            d = occ_g<OpSSNP>(threads);
-  return std::min(std::min(a, b), std::min(c, d));
+// CTAs per SM of the group solves of four or eight lanes (two = false) or of
+// two lanes (two = true)
+int occupancy_group(int threads, bool two) {
+  const int a = occ_g<OpSSSP>(threads, two), b = occ_g<OpSSWP>(threads, two), c = occ_g<OpBFS>(threads, two),
+            d = occ_g<OpSSNP>(threads, two), e = occ_g<OpMixed>(threads, two);
+  return std::min(std::min(std::min(a, b), std::min(c, d)), e);
 }
 
 }  // namespace svv

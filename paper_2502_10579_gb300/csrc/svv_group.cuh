@@ -30,22 +30,32 @@ namespace svv {
 // stale row gives worse candidates (see ld_val)
 template <int KL>
 __device__ __forceinline__ void ld_row(const uint32_t* p, uint32_t (&r)[KL]) {
-  const uint4* q = reinterpret_cast<const uint4*>(p);
+  if constexpr (KL == 2) {
+    const uint2 x = *reinterpret_cast<const uint2*>(p);
+    r[0] = x.x;
+    r[1] = x.y;
+  } else {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
 #pragma unroll
-  for (int i = 0; i < KL / 4; ++i) {
-    const uint4 x = q[i];
-    r[4 * i] = x.x;
-    r[4 * i + 1] = x.y;
-    r[4 * i + 2] = x.z;
-    r[4 * i + 3] = x.w;
+    for (int i = 0; i < KL / 4; ++i) {
+      const uint4 x = q[i];
+      r[4 * i] = x.x;
+      r[4 * i + 1] = x.y;
+      r[4 * i + 2] = x.z;
+      r[4 * i + 3] = x.w;
+    }
   }
 }
 
 template <int KL>
 __device__ __forceinline__ void st_row(uint32_t* p, const uint32_t (&r)[KL]) {
-  uint4* q = reinterpret_cast<uint4*>(p);
+  if constexpr (KL == 2) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(r[0], r[1]);
+  } else {
+    uint4* q = reinterpret_cast<uint4*>(p);
 #pragma unroll
-  for (int i = 0; i < KL / 4; ++i) q[i] = make_uint4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+    for (int i = 0; i < KL / 4; ++i) q[i] = make_uint4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+  }
 }
 
 // lanes in which an edge takes part: every lane for an edge present in all S
@@ -60,14 +70,15 @@ __device__ __forceinline__ uint32_t lanes_of(uint32_t word) {
 // source row `su`, against the target row at `xr`; returns true if some lane
 // of x was lowered (raised, for SSWP) by this edge
 template <class Op, int KL>
-__device__ __forceinline__ bool relax_lanes(const uint32_t (&su)[KL], uint32_t w, uint32_t pm, uint32_t* xr) {
+__device__ __forceinline__ bool relax_lanes(const uint32_t (&su)[KL], uint32_t w, uint32_t pm, uint32_t* xr,
+                                            uint32_t kinds) {
   uint32_t cur[KL];
   ld_row<KL>(xr, cur);
   bool imp = false;
 #pragma unroll
   for (int k = 0; k < KL; ++k) {
     if ((pm >> k) & 1u) {
-      const uint32_t cand = Op::relax(su[k], w);
+      const uint32_t cand = lane_relax<Op>(kinds, k, su[k], w);
       if (Op::better(cand, cur[k])) {
         Op::red(xr + k, cand);
         imp = true;
@@ -141,7 +152,7 @@ __device__ bool group_solve_team(const GroupArgs& a, const Team& t, unsigned lon
           x = e.x;
           uint32_t su[KL];
           ld_row<KL>(a.val + (size_t)u * KL, su);
-          if (relax_lanes<Op, KL>(su, e.y, pm, a.val + (size_t)x * KL) && atomicExch(a.stamp + x, 1u) != 1u) {
+          if (relax_lanes<Op, KL>(su, e.y, pm, a.val + (size_t)x * KL, a.kinds) && atomicExch(a.stamp + x, 1u) != 1u) {
             push = true;
             deg = __ldg(g.rp + x + 1) - __ldg(g.rp + x);
           }
@@ -183,6 +194,92 @@ __device__ bool group_solve_team(const GroupArgs& a, const Team& t, unsigned lon
     unsigned* qn_out = &c->qn[nxt];
     const uint32_t stamp_next = it + 1u;
 
+    if (pull && KL == 2 && !Op::kLevels) {
+      // ---- pull round of a two-lane group, as the single solve's: a warp
+      // takes 128 consecutive in-edges (4 per lane), the lowest lane of each
+      // target's run loads the target's row alongside the source gathers, and
+      // lanes with the same target fold their candidates lane by lane
+      uint32_t changed = 0, scanned = 0;
+      const uint32_t EF = g.E - g.NF;
+      const uint32_t ntot = EF + g.NF;
+      const uint32_t nchunks = (ntot + 127u) >> 7;
+      for (uint32_t ch = gwarp; ch < nchunks; ch += nwarps) {
+        uint32_t d[4], src[4], w[4], pm[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t idx = (ch << 7) + 32u * j + lane;
+          d[j] = 0xFFFFFFFFu - lane;  // unique per lane when not live
+          src[j] = 0;
+          w[j] = 0;
+          pm[j] = 0;
+          if (idx < ntot) {
+            if (idx < EF) {
+              d[j] = ld_stream(g.ifd + idx);
+              const uint2 sw = ld_stream(g.ifcw + idx);
+              src[j] = sw.x;
+              w[j] = sw.y;
+              pm[j] = allmask;
+            } else {
+              const uint32_t k = idx - EF;
+              d[j] = ld_stream(g.ipd + k);
+              const uint2 sw = ld_stream(g.ipcw + k);
+              src[j] = sw.x;
+              w[j] = sw.y;
+              pm[j] = lanes_of<PRED>(ld_stream(a.iplanes + k)) & allmask;
+            }
+          }
+        }
+        uint2 tv[4];
+        unsigned lead = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const unsigned grp = __match_any_sync(kFullMask, d[j]);
+          const uint32_t idx = (ch << 7) + 32u * j + lane;
+          const bool ld = idx < ntot && lane == (unsigned)(__ffs(grp) - 1);
+          lead |= (ld ? 1u : 0u) << j;
+          tv[j] = ld ? *reinterpret_cast<const uint2*>(a.val + (size_t)d[j] * 2) : make_uint2(0u, 0u);
+        }
+        uint32_t c0[4], c1[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          c0[j] = c1[j] = Op::kIdentity;
+          if (pm[j]) {
+            const uint2 su = *reinterpret_cast<const uint2*>(a.val + (size_t)src[j] * 2);
+            if (pm[j] & 1u) c0[j] = lane_relax<Op>(a.kinds, 0, su.x, w[j]);
+            if (pm[j] & 2u) c1[j] = lane_relax<Op>(a.kinds, 1, su.y, w[j]);
+          }
+          scanned += __popc(__ballot_sync(kFullMask, pm[j] != 0u));
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const unsigned grp = __match_any_sync(kFullMask, d[j]);
+          const uint32_t b0 = Op::better(0u, 1u) ? __reduce_min_sync(grp, c0[j]) : __reduce_max_sync(grp, c0[j]);
+          const uint32_t b1 = Op::better(0u, 1u) ? __reduce_min_sync(grp, c1[j]) : __reduce_max_sync(grp, c1[j]);
+          if ((lead >> j) & 1u) {
+            uint32_t* xr = a.val + (size_t)d[j] * 2;
+            bool imp = false;
+            if (Op::better(b0, tv[j].x)) {
+              Op::red(xr, b0);
+              imp = true;
+            }
+            if (Op::better(b1, tv[j].y)) {
+              Op::red(xr + 1, b1);
+              imp = true;
+            }
+            if (imp) {
+              // a plain store, as in the other pull rounds
+              a.stamp[d[j]] = stamp_next;
+              ++changed;
+            }
+          }
+        }
+      }
+      if (lane == 0) relaxed += scanned;
+      const uint32_t wc = __reduce_add_sync(kFullMask, changed);
+      if (lane == 0 && wc) atomicAdd(qn_out, wc);
+      if (!t.sync()) return false;
+      continue;
+    }
     if (pull) {
       // ---- pull round over the edge-flat transposed graph: each lane takes
       // two in-edges per step, computes every lane's candidate from the
@@ -249,7 +346,7 @@ __device__ bool group_solve_team(const GroupArgs& a, const Team& t, unsigned lon
             ld_row<KL>(a.val + (size_t)src[j] * KL, su);
 #pragma unroll
             for (int k = 0; k < KL; ++k)
-              if (((pm[j] >> k) & 1u) && (!bottom_up || su[k] < it)) cand[k] = Op::relax(su[k], w[j]);
+              if (((pm[j] >> k) & 1u) && (!bottom_up || su[k] < it)) cand[k] = lane_relax<Op>(a.kinds, k, su[k], w[j]);
           }
           scanned += __popc(__ballot_sync(kFullMask, pm[j] != 0u));
           const unsigned grp = __match_any_sync(kFullMask, d[j]);
@@ -359,7 +456,7 @@ __device__ bool group_solve_team(const GroupArgs& a, const Team& t, unsigned lon
               for (int k = 0; k < KL; ++k)
                 if (su[k] >= it) pm &= ~(1u << k);
             }
-            if (pm && relax_lanes<Op, KL>(su, ew.y, pm, a.val + (size_t)x * KL) &&
+            if (pm && relax_lanes<Op, KL>(su, ew.y, pm, a.val + (size_t)x * KL, a.kinds) &&
                 atomicExch(a.stamp + x, stamp_next) != stamp_next) {
               push = true;
               deg = __ldg(g.rp + x + 1) - __ldg(g.rp + x);

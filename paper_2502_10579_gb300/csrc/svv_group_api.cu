@@ -44,8 +44,22 @@ svv_status enqueue_group_bounds(svv_ctx* c, int t, const BatchInstance* inst, ui
   if (n < 1 || n > (uint32_t)kGroupMax) return fail(c, SVV_EINTERNAL, "group size out of range");
   svv_status st = ensure_group(c);
   if (st) return st;
-  const uint32_t KL = n <= 4 ? 4u : 8u;
+  const uint32_t KL = n <= 2 ? 2u : n <= 4 ? 4u : 8u;
   const Knobs kn = knobs_of(c, t, inst[0].wl);
+  // several types: every lane in the min lattice with its own relaxation
+  // kind, SSWP lanes complemented (undone by the split)
+  bool mixed = false;
+  for (uint32_t k = 1; k < n; ++k) mixed |= inst[k].type != inst[0].type;
+  uint32_t kinds = 0, flip = 0;
+  if (mixed) {
+    for (uint32_t k = 0; k < n; ++k) {
+      const int tk = inst[k].type;
+      const uint32_t kind = tk == 0 ? kKindSum : tk == 1 ? kKindMaxNot : tk == 2 ? kKindHop : kKindMax;
+      kinds |= kind << (2 * k);
+      if (tk == 1) flip |= 1u << k;
+    }
+  }
+  const int gt = mixed ? kTypeMixed : t;
   cudaError_t e = cudaMemsetAsync(c->ctl + 4, 0, sizeof(TeamCtl) * 2, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->qerr, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "memset");
@@ -88,18 +102,27 @@ svv_status enqueue_group_bounds(svv_ctx* c, int t, const BatchInstance* inst, ui
   }
   a.pull_units = pull_u[0];
   a.push_verts = push_v[0];
+  a.kinds = kinds;
   if (c->round_trace) {  // phases 0 and 1 of the round trace: the group's two solves
     cudaMemsetAsync(c->trace, 0, 2 * kTraceCap * sizeof(unsigned long long), s);
     a.trace = c->trace;
     a.trace_cap = kTraceCap;
   }
-  const LaunchCfg cfg = cfg_for(c, c->occ_group, kn.bps);
-  if ((e = launch_group_solve(t, KL, kPredAll, a, cfg, s)) != cudaSuccess)
+  const LaunchCfg cfg = cfg_for(c, KL == 2 ? c->occ_group2 : c->occ_group, kn.bps);
+  // phase timing of the group's two solves (read back after the batch)
+  bool timed = c->phase_timing && !c->graph_mode && !c->serve.active;
+  for (auto& ev : c->gev)
+    if (timed && !ev && cudaEventCreate(&ev) != cudaSuccess) timed = false;
+  if (timed) cudaEventRecord(c->gev[0], s);
+  c->gev_pending = timed;
+  if ((e = launch_group_solve(gt, KL, kPredAll, a, cfg, s)) != cudaSuccess)
     return cuda_fail(c, e, "launch group intersection solve");
+  if (timed) cudaEventRecord(c->gev[1], s);
   SplitArgs sp{};
   sp.V = c->g.V;
   sp.nlanes = n;
   sp.KL = KL;
+  sp.flip = flip;
   sp.cap = c->gcap;
   sp.cup = c->gcap;
   if (c->prune) {  // without pruning the union values are never read
@@ -111,10 +134,11 @@ svv_status enqueue_group_bounds(svv_ctx* c, int t, const BatchInstance* inst, ui
     b.pull_units = pull_u[1];
     b.push_verts = push_v[1];
     if (c->round_trace) b.trace = c->trace + kTraceCap;
-    if ((e = launch_group_solve(t, KL, kPredAny, b, cfg, s)) != cudaSuccess)
+    if ((e = launch_group_solve(gt, KL, kPredAny, b, cfg, s)) != cudaSuccess)
       return cuda_fail(c, e, "launch group union solve");
     sp.cup = c->gcup;
   }
+  if (timed) cudaEventRecord(c->gev[2], s);
   for (uint32_t k = 0; k < n; ++k) {
     sp.rI[k] = c->gI[k];
     sp.rU[k] = c->gU[k];

@@ -9,6 +9,10 @@ namespace svv {
 constexpr uint32_t kNone = 0xFFFFFFFFu;  // "no row": the vertex is stable
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kSat = 0xFFFFFFFEu;   // SSSP sums saturate here
+constexpr int kTypeMixed = 4;            // a query group of several types (group solves only)
+// relaxation kinds of a mixed group's lanes: Val(u)+w (SSSP), Val(u)+1 (BFS),
+// max(Val(u), w) (SSNP), max(Val(u), ~w) (SSWP on complemented widths)
+enum : uint32_t { kKindSum = 0, kKindHop = 1, kKindMax = 2, kKindMaxNot = 3 };
 
 // error codes written by kernels; numerically equal to svv_status values
 enum : uint32_t { kErrNone = 0, kErrTimeout = 4, kErrInternal = 7 };
@@ -273,6 +277,7 @@ struct GroupArgs {
   uint32_t maxit;
   unsigned long long spin_ns;
   uint32_t pull_units, push_verts;  // direction switch, as in SolveArgs
+  uint32_t kinds;                   // mixed-type groups: lane k's relaxation kind in bits 2k..2k+1
   unsigned long long* trace;
   uint32_t trace_cap;
 };
@@ -290,6 +295,7 @@ struct LanesArgs {
 // per-lane planar copies of the group's bound rows, for the per-query phases
 struct SplitArgs {
   uint32_t V, nlanes, KL;
+  uint32_t flip;                    // bit k: lane k holds complemented values (SSWP in a mixed group)
   const uint32_t* cap;
   const uint32_t* cup;
   uint32_t* rI[kGroupMax];
@@ -305,7 +311,7 @@ struct LaunchCfg {
 cudaError_t launch_group_lanes(const LanesArgs& a, cudaStream_t s);
 cudaError_t launch_group_solve(int type, uint32_t KL, int pred, const GroupArgs& a, LaunchCfg cfg, cudaStream_t s);
 cudaError_t launch_group_split(const SplitArgs& a, cudaStream_t s);
-int occupancy_group(int threads);
+int occupancy_group(int threads, bool two_lanes);
 
 cudaError_t launch_batch(const BatchArgs& b, LaunchCfg cfg, cudaStream_t s);
 int occupancy_batch(int threads);

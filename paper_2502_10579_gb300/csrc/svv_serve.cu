@@ -5,7 +5,8 @@
 // rounds fill the GPU, requests run in QUERY GROUPS (continuous batching): a
 // scheduler thread takes the submitted requests in arrival order and, each
 // time the group queued last has finished its bound solves, queues the next
-// group -- up to group_max pending requests of the oldest request's type --
+// group -- up to group_max pending requests of the oldest request's type (of
+// any type with group_mix) --
 // on the server's stream: one pair of group solves for the members' bounds
 // (one value lane per request, one set of frontier rounds), then each
 // member's own phases.  Requests that arrive while a group runs join the next
@@ -209,7 +210,7 @@ void sched_loop(svv_ctx* c) {
     } else {
       for (auto it = S.pending.begin(); it != S.pending.end() && grp.size() < c->group_max;) {
         const BatchInstance& q = v.h_inst[*it];
-        if (q.type == q0.type && !source_is_isolated(c, q.source)) {
+        if ((c->group_mix || q.type == q0.type) && !source_is_isolated(c, q.source)) {
           grp.push_back(*it);
           it = S.pending.erase(it);
         } else {

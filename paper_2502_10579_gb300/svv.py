@@ -55,7 +55,8 @@ class svv_stats(ctypes.Structure):
                 ("edges_relaxed_multi", ctypes.c_uint64), ("ms_cap", ctypes.c_float),
                 ("ms_cup", ctypes.c_float), ("ms_qrs", ctypes.c_float), ("ms_relax", ctypes.c_float),
                 ("ms_scatter", ctypes.c_float), ("ms_batch", ctypes.c_float),
-                ("batch_teams", ctypes.c_uint32), ("batch_team_blocks", ctypes.c_uint32)]
+                ("batch_teams", ctypes.c_uint32), ("batch_team_blocks", ctypes.c_uint32),
+                ("ms_group_cap", ctypes.c_float), ("ms_group_cup", ctypes.c_float)]
 
 
 _lib = None

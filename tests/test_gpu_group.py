@@ -58,6 +58,43 @@ def test_group_two_words_matches_oracle(svv, gmax):
             np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L))
 
 
+@pytest.mark.parametrize("gmax", [2, 4, 8])
+def test_mixed_type_groups_match_oracle(svv, gmax):
+    """group_mix: queries of every type share a group's rounds, each lane in
+    the min lattice with its own relaxation (SSWP on complemented widths);
+    two mask words, hub and random sources, every window length."""
+    log = W.scaled_rmat(scale=12, edge_factor=8, n_snapshots=100, rate=0.003, seed=37, add_mode="skewed")
+    specs = _specs(log, 24, 70 + gmax, hubs=np.concatenate([_hubs(log, 6), np.arange(6) * 97]))
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        ctx.set_tuning("group_mix", 1)
+        outs = _run(svv, ctx, specs, gmax)
+        for (t, s, b, L), o in zip(specs, outs):
+            np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L))
+
+
+@pytest.mark.parametrize("pull", [1, 0])
+def test_mixed_pair_same_source(svv, pull):
+    """An SSSP and an SSWP query from one hub over one window (two lanes, one
+    of them complemented), with and without pull rounds, equal the queries
+    alone and the oracle; weights up to 2^32 - 1 exercise the complement's
+    edge cases (a weight of 0 complements to the identity)."""
+    log = W.scaled_rmat(scale=14, edge_factor=16, n_snapshots=64, rate=0.001, seed=43)
+    big = W.random_small_log(29, V=300, n_edges=3000, S=20, n_add=20, n_del=20, w_lo=0, w_hi=(1 << 32) - 1)
+    for lg in (log, big):
+        src = int(_hubs(lg, 1)[0])
+        specs = [(0, src, 0, lg.S), (1, src, 0, lg.S), (3, src, 2, lg.S - 4), (2, src, 1, lg.S - 1)]
+        with svv.Context(0) as ctx:
+            ctx.set_tuning("pull", pull)
+            ctx.load_log(lg)
+            ctx.set_tuning("group_mix", 1)
+            for n in (2, 4):
+                outs = _run(svv, ctx, specs[:n], 8)
+                for (t, s, b, L), o in zip(specs[:n], outs):
+                    np.testing.assert_array_equal(svv.to_u32(o), oracle.query(lg, t, s, b, L))
+                    assert torch.equal(o, ctx.query(t, s, b, L))
+
+
 @pytest.mark.parametrize("pull", [1, 0])
 def test_group_hubs_equal_alone(svv, pull):
     """Deep solves from hub sources (pull rounds when the frontier is large,

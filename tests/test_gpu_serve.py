@@ -91,8 +91,8 @@ def test_serve_admission_and_relaunch(svv):
         svv.svv_serve_stop(ctx.h)
 
 
-@pytest.mark.parametrize("gmax", [8, 1])
-def test_serve_groups(svv, gmax):
+@pytest.mark.parametrize("gmax,mix", [(8, 0), (1, 0), (8, 1)])
+def test_serve_groups(svv, gmax, mix):
     """batch_mode 2 (the mode of graphs from 2M vertices): a scheduler queues
     the submitted requests in query groups of up to group_max same-type
     requests, formed each time the previous group has its bounds.  Requests
@@ -112,6 +112,7 @@ def test_serve_groups(svv, gmax):
         alone = [svv.to_u32(ctx.query(t, s, b, L)) for t, s, b, L in reqs]
         ctx.set_tuning("batch_mode", 2)
         ctx.set_tuning("group_max", gmax)
+        ctx.set_tuning("group_mix", mix)
         svv.svv_serve_start(ctx.h, max_window=100, capacity=64, arena_bytes=900 * log.V * 4)
         side = torch.cuda.Stream()
         pending, spans, refused = [], [], 0
