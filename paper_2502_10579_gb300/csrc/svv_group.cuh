@@ -338,6 +338,18 @@ __device__ bool group_solve_team(const GroupArgs& a, const Team& t, unsigned lon
             for (int k = 0; k < KL; ++k) open |= (dv[k] == kInf ? 1u : 0u) << k;
             pm[j] &= open;
           }
+          // the lowest lane of the target's run loads the target's row
+          // alongside the source row, not after the fold
+          const unsigned grp = __match_any_sync(kFullMask, d[j]);
+          const bool leader = idx < ntot && lane == (unsigned)(__ffs(grp) - 1);
+          uint32_t* xr = a.val + (size_t)d[j] * KL;
+          uint32_t cv[KL];
+          if (leader) {
+            ld_row<KL>(xr, cv);
+          } else {
+#pragma unroll
+            for (int k = 0; k < KL; ++k) cv[k] = Op::kIdentity;
+          }
           uint32_t cand[KL];
 #pragma unroll
           for (int k = 0; k < KL; ++k) cand[k] = Op::kIdentity;
@@ -349,16 +361,12 @@ __device__ bool group_solve_team(const GroupArgs& a, const Team& t, unsigned lon
               if (((pm[j] >> k) & 1u) && (!bottom_up || su[k] < it)) cand[k] = lane_relax<Op>(a.kinds, k, su[k], w[j]);
           }
           scanned += __popc(__ballot_sync(kFullMask, pm[j] != 0u));
-          const unsigned grp = __match_any_sync(kFullMask, d[j]);
           uint32_t best[KL];
 #pragma unroll
           for (int k = 0; k < KL; ++k)
             best[k] = Op::better(0u, 1u) ? __reduce_min_sync(grp, cand[k]) : __reduce_max_sync(grp, cand[k]);
           const bool any = __reduce_or_sync(grp, pm[j]) != 0u;
-          if (idx < ntot && any && lane == (unsigned)(__ffs(grp) - 1)) {
-            uint32_t* xr = a.val + (size_t)d[j] * KL;
-            uint32_t cv[KL];
-            ld_row<KL>(xr, cv);
+          if (leader && any) {
             bool imp = false;
 #pragma unroll
             for (int k = 0; k < KL; ++k) {
