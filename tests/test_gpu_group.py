@@ -95,6 +95,25 @@ def test_mixed_pair_same_source(svv, pull):
                     assert torch.equal(o, ctx.query(t, s, b, L))
 
 
+@pytest.mark.parametrize("pair", [(0, 1), (1, 1), (3, 3), (0, 3), (1, 2)])
+def test_two_lane_groups_pull_every_round(svv, pair):
+    """Two-lane groups (their own pull loop: four in-edges per lane, the run
+    leader's target row loaded with the source rows), with both group solves
+    pulling nearly every round; same-type pairs in their own lattice (SSWP's
+    max lattice included) and mixed pairs in the min lattice."""
+    log = W.scaled_rmat(scale=13, edge_factor=16, n_snapshots=70, rate=0.002, seed=47, add_mode="skewed")
+    hubs = _hubs(log, 3)
+    specs = [(pair[0], int(hubs[0]), 0, 70), (pair[1], int(hubs[1]), 5, 60)]
+    with svv.Context(0) as ctx:
+        ctx.load_log(log)
+        ctx.set_tuning("group_mix", 1)
+        ctx.set_tuning("group_pull_pct", 1)
+        ctx.set_tuning("group_pull_pct_union", 1)
+        outs = _run(svv, ctx, specs, 2)
+        for (t, s, b, L), o in zip(specs, outs):
+            np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L))
+
+
 @pytest.mark.parametrize("pull", [1, 0])
 def test_group_hubs_equal_alone(svv, pull):
     """Deep solves from hub sources (pull rounds when the frontier is large,
