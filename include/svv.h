@@ -395,7 +395,10 @@ svv_status svv_autotune(svv_ctx *ctx, svv_type type, uint32_t source, uint32_t w
  * default: a group holds queries of one type; 1: queries of any types share a
  * group, every lane solved in the min lattice with its own relaxation --
  * SSWP lanes on complemented widths, converted back when the bounds are
- * split -- results identical), "group_pull_pct" /
+ * split -- results identical), "pair_tails" (1 default: a two-query group
+ * with device outputs whose windows have one length of at most 128 snapshots
+ * relaxes both queries in one launch over both queries' rows; 0 relaxes them
+ * one after the other; results identical), "group_pull_pct" /
  * "group_pull_pct_union" (0..100, defaults 15 / 100: a group's intersection /
  * union solve pulls when its frontier holds more than this % of all work
  * units; 0 or 100 = push only), "isolated_fast" (1 default: a query whose

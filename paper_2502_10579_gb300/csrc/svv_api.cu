@@ -21,6 +21,7 @@ void free_graph(svv_ctx* c) {
   free_serve(c);
   free_batch(c);
   free_group(c);
+  free_pair(c);
   free_list(c, c->graph_bufs);
   free_list(c, c->scratch_bufs);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
@@ -304,6 +305,9 @@ svv_status svv_set_tuning(svv_ctx* c, const char* key, int64_t v) {
   } else if (k == "batch_mode") {
     if (v < 0 || v > 2) return fail(c, SVV_EINVAL, "batch_mode is 0 (by graph size), 1 (one launch) or 2 (in order)");
     c->batch_mode = (int)v;
+  } else if (k == "pair_tails") {
+    if (v < 0 || v > 1) return fail(c, SVV_EINVAL, "pair_tails: 0 or 1");
+    c->pair_tails = v != 0;
   } else if (k == "group_mix") {
     if (v < 0 || v > 1) return fail(c, SVV_EINVAL, "group_mix: 0 or 1");
     c->group_mix = v != 0;
@@ -712,6 +716,7 @@ svv_status enqueue_tail(svv_ctx* c, int t, uint32_t wb, uint32_t wl, uint32_t* o
   q.qmask = c->qmask;
   q.ecap = c->ecap;
   q.mcap = c->mcap;
+  q.rowcap = c->g.V;
   q.ctl = c->ctl + 2;
   q.qerr = c->qerr;
   q.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
@@ -941,8 +946,14 @@ svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, con
   cudaStream_t es = s;
   bool capture = c->graph_mode && !host_out && !c->round_trace;
   if (capture) {
-    for (const auto& grp : groups)
+    for (const auto& grp : groups) {
       if (grp.size() > 1 && (st = ensure_group(c))) return st;
+      if (grp.size() == 2 && c->pair_tails && inst[grp[0]].wl == inst[grp[1]].wl && inst[grp[0]].wl <= kMaxSlab) {
+        uint32_t P, K;
+        slab_shape_p(inst[grp[0]].wl, knobs_of(c, inst[grp[0]].type, inst[grp[0]].wl).relax_lanes, P, K);
+        if ((st = ensure_pair_rows(c, P * K))) return st;
+      }
+    }
     if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       capture = false;
@@ -992,6 +1003,27 @@ svv_status batch_in_order(svv_ctx* c, const BatchInstance* inst, uint32_t m, con
       for (size_t j = 0; j < grp.size(); ++j) gi[j] = inst[grp[j]];
       if ((st = enqueue_group_bounds(c, gi[0].type, gi, (uint32_t)grp.size(), es)))
         return capture ? end_capture(st) : st;
+      // a pair with device outputs: both tails with one relaxation launch
+      if (grp.size() == 2 && !(host_out && (host_out[grp[0]] || host_out[grp[1]]))) {
+        uint32_t* po[2] = {inst[grp[0]].out, inst[grp[1]].out};
+        const uint32_t* pI[2] = {c->gI[0], c->gI[1]};
+        const uint32_t* pU[2] = {c->gU[0], c->gU[1]};
+        bool done = false;
+        if ((e = cudaMemcpyAsync(c->qerr, c->gerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, es)) != cudaSuccess)
+          st = cuda_fail(c, e, "group status copy");
+        else
+          st = enqueue_pair_tail(c, gi, po, pI, pU, es, &done);
+        if (st) return capture ? end_capture(st) : st;
+        if (done) {
+          for (int j = 0; j < 2; ++j)
+            if ((e = cudaMemcpyAsync(qerr_dev + grp[j], c->qerr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, es)) !=
+                cudaSuccess) {
+              st = cuda_fail(c, e, "batch status copy");
+              return capture ? end_capture(st) : st;
+            }
+          continue;
+        }
+      }
     }
     for (size_t j = 0; j < grp.size(); ++j) {
       const uint32_t k = grp[j];

@@ -131,6 +131,7 @@ __device__ bool run_instance(const BatchArgs& b, const BatchInstance& q, uint32_
   r.qmask = sc.qmask;
   r.ecap = sc.ecap;
   r.mcap = sc.mcap;
+  r.rowcap = b.g.V;
   r.ctl = tc + 3;
   r.qerr = t.qerr;
   r.spin_ns = b.spin_ns;

@@ -181,6 +181,17 @@ struct svv_ctx {
   uint64_t valcap = 0;
   uint32_t* staging = nullptr;  // device output for svv_query_host
   uint64_t staging_cap = 0;
+  // a two-query group's tails in one relaxation launch: both queries' rows,
+  // subgraph edges and masks in one set of arrays (allocated on first use)
+  std::vector<void*> pair_bufs;
+  uint32_t *p_uv = nullptr, *p_qcnt = nullptr, *p_cur = nullptr, *p_stamp = nullptr, *p_row1 = nullptr;
+  uint4* p_qrow = nullptr;
+  uint2* p_qcw = nullptr;
+  uint64_t* p_qmask = nullptr;
+  uint32_t* p_val = nullptr;
+  unsigned long long *p_q0 = nullptr, *p_q1 = nullptr;
+  uint64_t p_valcap = 0, p_qcap = 0;
+  bool pair_tails = true;  // run a two-query group's relaxations in one launch
   // svv_query_batch with host outputs: two staging slots and a copy stream
   uint32_t* bstage[2] = {nullptr, nullptr};
   uint64_t bstage_cap = 0;      // words per slot
@@ -338,6 +349,12 @@ svv_status enqueue_isolated(svv_ctx* c, int t, uint32_t source, uint32_t wl, uin
 svv_status enqueue_tail(svv_ctx* c, int t, uint32_t wb, uint32_t wl, uint32_t* out, const uint32_t* rI,
                         const uint32_t* rU, cudaStream_t s, bool timing, float* ms_relax_out, float* ms_scatter_out,
                         const CompactOut* co, bool fresh);
+// the tails of a two-query group (same window length, one slab) with one
+// relaxation launch; false in *done when the pair does not qualify
+svv_status enqueue_pair_tail(svv_ctx* c, const svv::BatchInstance* inst, uint32_t* const* out,
+                             const uint32_t* const* rI, const uint32_t* const* rU, cudaStream_t s, bool* done);
+void free_pair(svv_ctx* c);
+svv_status ensure_pair_rows(svv_ctx* c, uint32_t LP);  // the pair arrays for rows of LP values
 
 // query groups (svv_group_api.cu): the bounds of up to group_max same-type
 // queries from one pair of group solves, then each query's own phases

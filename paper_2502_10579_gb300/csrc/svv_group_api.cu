@@ -149,4 +149,151 @@ svv_status enqueue_group_bounds(svv_ctx* c, int t, const BatchInstance* inst, ui
   return SVV_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Two-query tails.  The first query's stable compaction and subgraph go to
+// rows [0, U0) of the pair arrays, the second's after them (its extraction
+// reads the first query's counts on the device); one relaxation launch then
+// runs Algorithm 2 over both queries' rows with one frontier, and each query's
+// scatter reads its own rows.  A pair of different types relaxes in the min
+// lattice (OpMixed), an SSWP query's rows on complemented widths.
+
+void free_pair(svv_ctx* c) {
+  for (void* p : c->pair_bufs) cudaFree(p);
+  c->pair_bufs.clear();
+  c->p_uv = c->p_qcnt = c->p_cur = c->p_stamp = c->p_row1 = nullptr;
+  c->p_qrow = nullptr;
+  c->p_qcw = nullptr;
+  c->p_qmask = nullptr;
+  c->p_val = nullptr;
+  c->p_q0 = c->p_q1 = nullptr;
+  c->p_valcap = c->p_qcap = 0;
+}
+
+svv_status ensure_pair_rows(svv_ctx* c, uint32_t LP) {
+  const uint64_t V = c->g.V;
+  const uint64_t need_v = 2 * V * LP;
+  if (c->p_uv && need_v <= c->p_valcap) return SVV_OK;
+  free_pair(c);
+  // every array holds two queries' worth of what the single-query scratch holds
+  svv_status st;
+  if ((st = alloc_n(c, c->pair_bufs, 2 * V, &c->p_uv)) || (st = alloc_n(c, c->pair_bufs, 4 * V, &c->p_qcnt)) ||
+      (st = alloc_n(c, c->pair_bufs, 4 * V, &c->p_cur)) || (st = alloc_n(c, c->pair_bufs, 2 * V, &c->p_stamp)) ||
+      (st = alloc_n(c, c->pair_bufs, V, &c->p_row1)) || (st = alloc_n(c, c->pair_bufs, 2 * V, &c->p_qrow)) ||
+      (st = alloc_n(c, c->pair_bufs, 2 * (uint64_t)c->ecap, &c->p_qcw)) ||
+      (st = alloc_n(c, c->pair_bufs, 2 * c->mcap, &c->p_qmask)) ||
+      (st = alloc_n(c, c->pair_bufs, need_v, &c->p_val)) ||
+      (st = alloc_n(c, c->pair_bufs, 2 * (uint64_t)c->qcap, &c->p_q0)) ||
+      (st = alloc_n(c, c->pair_bufs, 2 * (uint64_t)c->qcap, &c->p_q1))) {
+    free_pair(c);
+    return st;
+  }
+  c->p_valcap = need_v;
+  c->p_qcap = 2 * (uint64_t)c->qcap;
+  return SVV_OK;
+}
+
+svv_status enqueue_pair_tail(svv_ctx* c, const BatchInstance* inst, uint32_t* const* out, const uint32_t* const* rI,
+                             const uint32_t* const* rU, cudaStream_t s, bool* done) {
+  *done = false;
+  const uint32_t wl = inst[0].wl;
+  if (!c->pair_tails || inst[1].wl != wl || wl > kMaxSlab) return SVV_OK;
+  const Knobs k0 = knobs_of(c, inst[0].type, wl), k1 = knobs_of(c, inst[1].type, wl);
+  if (wl > std::max<uint32_t>(1, std::min(k0.slab_max, kMaxSlab)) ||
+      wl > std::max<uint32_t>(1, std::min(k1.slab_max, kMaxSlab)) || k0.relax_lanes != k1.relax_lanes)
+    return SVV_OK;
+  uint32_t P, K;
+  slab_shape_p(wl, k0.relax_lanes, P, K);
+  svv_status st = ensure_pair_rows(c, P * K);
+  if (st) return st;
+  if (c->p_qcap > 0xFFFFFFFFull) return SVV_OK;
+  cudaError_t e = cudaMemsetAsync(c->ctl + 2, 0, sizeof(TeamCtl) * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl + 6, 0, sizeof(TeamCtl), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+  const uint32_t QW = ceil_div(wl, 64);
+  for (int qi = 0; qi < 2; ++qi) {
+    QrsArgs q{};
+    q.g = c->g;
+    q.win = Window{inst[qi].wb, wl};
+    q.QW = QW;
+    q.prune = c->prune ? 1 : 0;
+    q.rI = rI[qi];
+    q.rU = rU[qi];
+    q.row = qi ? c->p_row1 : c->row;
+    q.uv = c->p_uv;
+    q.part = c->part;
+    q.units = c->units;
+    q.ucap = c->ucap;
+    q.cshift = c->qrs_cs;
+    q.qcnt = c->p_qcnt;
+    q.qrow = c->p_qrow;
+    q.cur = c->p_cur;
+    q.qcw = c->p_qcw;
+    q.qmask = c->p_qmask;
+    q.ecap = (uint32_t)std::min<uint64_t>(2 * (uint64_t)c->ecap, 0xFFFFFFFFull);
+    q.mcap = 2 * c->mcap;
+    q.rowcap = 2 * c->g.V;
+    q.ctl = qi ? c->ctl + 6 : c->ctl + 2;
+    q.base = qi ? &(c->ctl + 2)->aux[0] : nullptr;
+    q.qerr = c->qerr;
+    q.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
+    LaunchCfg qc = cfg_for(c, c->occ_qrs, k0.bps);
+    if ((int64_t)qc.blocks > (int64_t)c->num_sms * 4) qc.blocks = c->num_sms * 4;
+    if ((e = launch_qrs(q, qc, s)) != cudaSuccess) return cuda_fail(c, e, "launch subgraph extraction");
+  }
+  const bool mixed = inst[0].type != inst[1].type;
+  auto kind_of = [](int t) { return t == 0 ? kKindSum : t == 1 ? kKindMaxNot : t == 2 ? kKindHop : kKindMax; };
+  RelaxArgs r{};
+  r.g = c->g;
+  r.win = Window{inst[0].wb, wl};
+  r.win1 = Window{inst[1].wb, wl};
+  r.s0 = 0;
+  r.ls = wl;
+  r.QW = QW;
+  r.rI = rI[0];
+  r.rI1 = rI[1];
+  r.row = c->row;
+  r.row1 = c->p_row1;
+  r.uv = c->p_uv;
+  r.qrow = c->p_qrow;
+  r.qcw = c->p_qcw;
+  r.qmask = c->p_qmask;
+  r.counts = &(c->ctl + 2)->aux[0];
+  r.counts1 = &(c->ctl + 6)->aux[0];
+  if (mixed) {
+    r.kind0 = kind_of(inst[0].type);
+    r.kind1 = kind_of(inst[1].type);
+    r.flip = (inst[0].type == 1 ? 1u : 0u) | (inst[1].type == 1 ? 2u : 0u);
+  }
+  r.val = c->p_val;
+  r.LP = P * K;
+  r.stamp = c->p_stamp;
+  r.q0 = c->p_q0;
+  r.q1 = c->p_q1;
+  r.qcap = (uint32_t)c->p_qcap;
+  r.cshift = c->relax_cs;
+  r.ctl = c->ctl + 3;
+  r.qerr = c->qerr;
+  r.maxit = c->maxit ? c->maxit : 2 * c->g.V + 2u;
+  r.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
+  if ((e = launch_relax(mixed ? kTypeMixed : inst[0].type, P, K, r, cfg_for(c, c->occ_relax, k0.bps), s)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "launch paired relaxation");
+  for (int qi = 0; qi < 2; ++qi) {
+    ScatterArgs sa{};
+    sa.V = c->g.V;
+    sa.s0 = 0;
+    sa.ls = wl;
+    sa.rI = rI[qi];
+    sa.row = qi ? c->p_row1 : c->row;
+    sa.val = c->p_val;
+    sa.LP = P * K;
+    sa.out = out[qi];
+    sa.qerr = c->qerr;
+    sa.rflip = ((r.flip >> qi) & 1u) ? 0xFFFFFFFFu : 0u;
+    if ((e = launch_scatter(sa, s)) != cudaSuccess) return cuda_fail(c, e, "launch scatter");
+  }
+  *done = true;
+  return SVV_OK;
+}
+
 }  // namespace svv

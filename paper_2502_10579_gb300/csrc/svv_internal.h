@@ -133,6 +133,11 @@ struct QrsArgs {
   uint32_t* qerr;
   unsigned long long spin_ns;
   unsigned long long* trace;  // optional: start ns of each of the five passes, then the end
+  // null, or the counts (aux) of a query extracted before into the same
+  // arrays: this query's rows, edges and masks then follow that query's
+  // (two queries relaxed in one launch)
+  const unsigned int* base;
+  uint32_t rowcap;        // rows the row arrays hold (uv, qrow; qcnt and cur hold 2 per row)
 };
 
 struct RelaxArgs {
@@ -147,6 +152,16 @@ struct RelaxArgs {
   const uint2* qcw;
   const uint64_t* qmask;
   const unsigned int* counts;  // qrs team aux: [0]=U
+  // a second query relaxed in the same launch (counts1 null: none): its rows
+  // follow the first query's, its subgraph edges point at rows of either
+  // range only within its own; same window length and slab
+  const unsigned int* counts1;
+  const uint32_t* rI1;
+  const uint32_t* row1;
+  Window win1;
+  // a pair of different types (OpMixed): each query's relaxation kind, and
+  // bit q set when query q's rows hold complemented values (SSWP)
+  uint32_t kind0, kind1, flip;
   uint32_t* val;          // [U * LP]
   uint32_t LP;            // row stride of val (>= ls)
   uint32_t* stamp;        // [V]
@@ -197,6 +212,7 @@ struct ScatterArgs {
   uint32_t LP;
   uint32_t* out;          // [win.l * V]; rows s0.. of this pass
   const uint32_t* qerr;
+  uint32_t rflip;         // XORed into every row value (complemented rows of a mixed pair)
 };
 
 // ---------------------------------------------------------------------------

@@ -187,6 +187,14 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
   if (cta_read(a.qerr) != 0u) return false;
   const uint32_t V = g.V;
   const uint32_t C = 1u << a.cshift;
+  // where this query's rows, edges and masks start (after a query extracted
+  // before into the same arrays)
+  uint32_t rbase = 0, ebase = 0, mbase = 0;
+  if (a.base) {
+    rbase = ld_cg(a.base + 0);
+    ebase = ld_cg(a.base + 2);
+    mbase = ld_cg(a.base + 3);
+  }
 
   // ---- P1: unstable vertices and their units, per CTA vertex range
   if (a.trace && b == 0 && tid == 0) a.trace[0] = global_ns();
@@ -230,7 +238,7 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
       c->aux[0] = U;
       c->aux[1] = NU;
     }
-    if (NU > a.ucap) {
+    if (NU > a.ucap || (unsigned long long)rbase + U > a.rowcap) {
       if (tid == 0) set_err(c, a.qerr, kErrInternal);
       return false;  // every CTA sees the same totals and leaves here
     }
@@ -243,7 +251,7 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
       }
       uint32_t ef, eu, tf, tu;
       block_excl_scan2(flag, nu, ef, eu, tf, tu);
-      const uint32_t r = o_r + ef;
+      const uint32_t r = rbase + o_r + ef;
       if (v < hi) {
         a.row[v] = flag ? r : kNone;
         if (flag) {
@@ -279,8 +287,8 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
   // ---- P4: scan rows
   if (a.trace && b == 0 && tid == 0) a.trace[3] = global_ns();
   const unsigned long long rper = (((unsigned long long)U + nb - 1) / nb + 31ull) & ~31ull;
-  const uint32_t rlo = (uint32_t)min((unsigned long long)U, rper * b);
-  const uint32_t rhi = (uint32_t)min((unsigned long long)U, rper * b + rper);
+  const uint32_t rlo = rbase + (uint32_t)min((unsigned long long)U, rper * b);
+  const uint32_t rhi = rbase + (uint32_t)min((unsigned long long)U, rper * b + rper);
   {
     uint32_t se = 0, sm = 0, z0 = 0, z1 = 0;
     for (uint32_t r = rlo + tid; r < rhi; r += blockDim.x) {
@@ -311,7 +319,7 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
       c->aux[2] = t_e;
       c->aux[3] = t_m;
     }
-    if (t_e > a.ecap || (unsigned long long)t_m * a.QW > a.mcap) {
+    if ((unsigned long long)ebase + t_e > a.ecap || ((unsigned long long)mbase + t_m) * a.QW > a.mcap) {
       if (tid == 0) set_err(c, a.qerr, kErrInternal);
       return false;
     }
@@ -325,8 +333,8 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
       uint32_t ee, em, te, tm;
       block_excl_scan2(f + m, m, ee, em, te, tm);
       if (r < rhi) {
-        const uint32_t start = o_e + ee;
-        a.qrow[r] = make_uint4(start, start + f, o_m + em, start + f + m);
+        const uint32_t start = ebase + o_e + ee;
+        a.qrow[r] = make_uint4(start, start + f, mbase + o_m + em, start + f + m);
         a.cur[2 * r] = start;
         a.cur[2 * r + 1] = start + f;
       }

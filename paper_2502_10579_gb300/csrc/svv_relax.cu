@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(ScatterArgs a)
       for (uint32_t i = lane; i < a.ls; i += 32u) {
         uint32_t y[4];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) y[h] = r[h] == kNone ? x[h] : a.val[((size_t)r[h] << lps) + i];
+        for (int h = 0; h < 4; ++h) y[h] = r[h] == kNone ? x[h] : (a.val[((size_t)r[h] << lps) + i] ^ a.rflip);
 #pragma unroll
         for (int h = 0; h < 4; ++h) tile[i * kTV + ((t0 + h) ^ (i & 31u))] = y[h];
       }
@@ -208,6 +208,7 @@ cudaError_t launch_relax(int type, uint32_t P, uint32_t K, const RelaxArgs& a, L
     case 0: return launch_pk<OpSSSP>(P, K, a, cfg, s);
     case 1: return launch_pk<OpSSWP>(P, K, a, cfg, s);
     case 3: return launch_pk<OpSSNP>(P, K, a, cfg, s);
+    case kTypeMixed: return launch_pk<OpMixed>(P, K, a, cfg, s);
     default: return launch_pk<OpBFS>(P, K, a, cfg, s);
   }
 }
@@ -244,10 +245,11 @@ static int occ_op(int threads) {
 
 int occupancy_relax(int threads) {
   int a = occ_op<OpSSSP>(threads), b = occ_op<OpSSWP>(threads), c = occ_op<OpBFS>(threads);
-  int d = occ_op<OpSSNP>(threads);
+  int d = occ_op<OpSSNP>(threads), e = occ_op<OpMixed>(threads);
   int m = a < b ? a : b;
   m = m < c ? m : c;
-  return m < d ? m : d;
+  m = m < d ? m : d;
+  return m < e ? m : e;
 }
 
 }  // namespace svv

@@ -8,6 +8,13 @@
 
 namespace svv {
 
+// query q's relaxation: the op's own, or (a mixed pair) query q's kind
+template <class Op>
+__device__ __forceinline__ uint32_t relax_q(const RelaxArgs& a, bool q1, uint32_t sv, uint32_t w) {
+  if constexpr (is_mixed<Op>::value) return OpMixed::relax_kind(q1 ? a.kind1 : a.kind0, sv, w);
+  else return Op::relax(sv, w);
+}
+
 template <class Op, int P, int K>
 __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long* stage) {
   const DevGraph& g = a.g;
@@ -18,17 +25,19 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
   const unsigned gwarp = gtid >> 5, nwarps = nthreads >> 5;
   if (cta_read(a.qerr) != 0u) return false;
   PushStage st{stage + (threadIdx.x >> 5) * kStageUnits, 0u};
-  const uint32_t U = a.counts[0];
+  // rows [0, U0) are the first query's, [U0, U) a second query's (a.counts1)
+  const uint32_t U0 = a.counts[0];
+  const uint32_t U = U0 + (a.counts1 ? a.counts1[0] : 0u);
   const uint32_t LP = a.LP;
   const uint32_t lps = __ffs(LP) - 1;  // LP is a power of two
-  const uint32_t snap0 = a.win.b + a.s0;  // absolute snapshot of slab column 0
 
   // ---- round 0a: values and stamps.  A warp reads the starting values of
   // 32 rows at once (a lane per row), then writes those rows together (a
   // lane per column), so the dependent loads are paid once per 32 rows.
   for (uint32_t r0 = gwarp * 32u; r0 < U; r0 += nwarps * 32u) {
     const uint32_t r = r0 + lane;
-    const uint32_t x = r < U ? a.rI[a.uv[r]] : 0u;
+    const uint32_t x = r < U ? ((r < U0 ? a.rI : a.rI1)[a.uv[r]] ^ ((a.flip >> (r < U0 ? 0 : 1)) & 1u ? ~0u : 0u))
+                             : 0u;
     if (r < U) a.stamp[r] = 0u;
     const uint32_t nr = min(32u, U - r0);
     for (uint32_t k = 0; k < nr; ++k) {
@@ -42,90 +51,98 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
 
   // ---- round 0b: seed from addition edges with an unstable sink; four
   // qualifying edges per warp iteration, lanes over the slab's snapshots
-  for (uint32_t k0 = gwarp * 32u; k0 < g.NF; k0 += nwarps * 32u) {
-    const uint32_t k = k0 + lane;
-    bool qual = false;
-    uint32_t rx = kNone, cand = 0;
-    if (k < g.NF) {
-      const uint2 e = __ldg(g.nfcw + k);
-      rx = a.row[e.x];
-      if (rx != kNone) {
-        bool any, all;
-        window_any_all(g.nfmask + (size_t)k * g.W, a.win, any, all);
-        qual = any && !all;
-        if (qual) cand = Op::relax(a.rI[__ldg(g.nfsrc + k)], e.y);
-      }
-    }
-    // the owner lane extracts the slab's presence bits once; the warp then
-    // takes four qualifying edges at a time with the bits in registers
-    uint64_t mlo = 0ull, mhi = 0ull;
-    if (qual) {
-      const uint64_t* mp = g.nfmask + (size_t)k * g.W;
-      mlo = mask_extract(mp, g.W, snap0);
-      if (a.ls > 64u) mhi = mask_extract(mp, g.W, snap0 + 64u);
-    }
-    unsigned bq = __ballot_sync(kFullMask, qual);
-    constexpr int HS = 4;
-    while (bq) {
-      int j[HS];
-#pragma unroll
-      for (int h = 0; h < HS; ++h) {
-        j[h] = bq ? __ffs(bq) - 1 : -1;
-        if (bq) bq &= bq - 1u;
-      }
-      uint32_t ex[HS], ec[HS];
-      uint64_t ml[HS], mh[HS];
-#pragma unroll
-      for (int h = 0; h < HS; ++h) {
-        const int src = j[h] < 0 ? j[0] : j[h];
-        ex[h] = __shfl_sync(kFullMask, rx, src);
-        ec[h] = __shfl_sync(kFullMask, cand, src);
-        ml[h] = __shfl_sync(kFullMask, mlo, src);
-        mh[h] = __shfl_sync(kFullMask, mhi, src);
-      }
-      bool imp[HS];
-#pragma unroll
-      for (int h = 0; h < HS; ++h) imp[h] = false;
-      for (uint32_t i = lane; i < a.ls; i += 32u) {
-        bool want[HS];
-        uint32_t curv[HS];
-#pragma unroll
-        for (int h = 0; h < HS; ++h) {
-          const uint64_t bit = i < 64u ? (ml[h] >> i) : (mh[h] >> (i - 64u));
-          want[h] = j[h] >= 0 && (bit & 1ull);
-          curv[h] = want[h] ? ld_val(a.val + ((size_t)ex[h] << lps) + i) : 0u;
+  // each query's seeds (the second query's rows map to its own range)
+  for (int qi = 0; qi < (a.counts1 ? 2 : 1); ++qi) {
+    const uint32_t* srow = qi ? a.row1 : a.row;
+    const uint32_t* srI = qi ? a.rI1 : a.rI;
+    const Window swin = qi ? a.win1 : a.win;
+    const uint32_t ssnap = swin.b + a.s0;
+    const uint32_t sflip = ((a.flip >> qi) & 1u) ? ~0u : 0u;
+    for (uint32_t k0 = gwarp * 32u; k0 < g.NF; k0 += nwarps * 32u) {
+      const uint32_t k = k0 + lane;
+      bool qual = false;
+      uint32_t rx = kNone, cand = 0;
+      if (k < g.NF) {
+        const uint2 e = __ldg(g.nfcw + k);
+        rx = srow[e.x];
+        if (rx != kNone) {
+          bool any, all;
+          window_any_all(g.nfmask + (size_t)k * g.W, swin, any, all);
+          qual = any && !all;
+          if (qual) cand = relax_q<Op>(a, qi != 0, srI[__ldg(g.nfsrc + k)] ^ sflip, e.y);
         }
-#pragma unroll
+      }
+      // the owner lane extracts the slab's presence bits once; the warp then
+      // takes four qualifying edges at a time with the bits in registers
+      uint64_t mlo = 0ull, mhi = 0ull;
+      if (qual) {
+        const uint64_t* mp = g.nfmask + (size_t)k * g.W;
+        mlo = mask_extract(mp, g.W, ssnap);
+        if (a.ls > 64u) mhi = mask_extract(mp, g.W, ssnap + 64u);
+      }
+      unsigned bq = __ballot_sync(kFullMask, qual);
+      constexpr int HS = 4;
+      while (bq) {
+        int j[HS];
+  #pragma unroll
         for (int h = 0; h < HS; ++h) {
-          if (want[h] && Op::better(ec[h], curv[h])) {
-            Op::red(a.val + ((size_t)ex[h] << lps) + i, ec[h]);
-            imp[h] = true;
+          j[h] = bq ? __ffs(bq) - 1 : -1;
+          if (bq) bq &= bq - 1u;
+        }
+        uint32_t ex[HS], ec[HS];
+        uint64_t ml[HS], mh[HS];
+  #pragma unroll
+        for (int h = 0; h < HS; ++h) {
+          const int src = j[h] < 0 ? j[0] : j[h];
+          ex[h] = __shfl_sync(kFullMask, rx, src);
+          ec[h] = __shfl_sync(kFullMask, cand, src);
+          ml[h] = __shfl_sync(kFullMask, mlo, src);
+          mh[h] = __shfl_sync(kFullMask, mhi, src);
+        }
+        bool imp[HS];
+  #pragma unroll
+        for (int h = 0; h < HS; ++h) imp[h] = false;
+        for (uint32_t i = lane; i < a.ls; i += 32u) {
+          bool want[HS];
+          uint32_t curv[HS];
+  #pragma unroll
+          for (int h = 0; h < HS; ++h) {
+            const uint64_t bit = i < 64u ? (ml[h] >> i) : (mh[h] >> (i - 64u));
+            want[h] = j[h] >= 0 && (bit & 1ull);
+            curv[h] = want[h] ? ld_val(a.val + ((size_t)ex[h] << lps) + i) : 0u;
+          }
+  #pragma unroll
+          for (int h = 0; h < HS; ++h) {
+            if (want[h] && Op::better(ec[h], curv[h])) {
+              Op::red(a.val + ((size_t)ex[h] << lps) + i, ec[h]);
+              imp[h] = true;
+            }
           }
         }
-      }
-      // lane h claims edge h's target (the HS stamp exchanges run side by
-      // side) and one warp append queues every claimed row
-      unsigned anyb = 0;
-#pragma unroll
-      for (int h = 0; h < HS; ++h) anyb |= (__any_sync(kFullMask, imp[h]) ? 1u : 0u) << h;
-      uint32_t px = 0;
-      bool claim = false;
-#pragma unroll
-      for (int h = 0; h < HS; ++h)
-        if (lane == (unsigned)h) {
-          px = ex[h];
-          claim = (anyb >> h) & 1u;
+        // lane h claims edge h's target (the HS stamp exchanges run side by
+        // side) and one warp append queues every claimed row
+        unsigned anyb = 0;
+  #pragma unroll
+        for (int h = 0; h < HS; ++h) anyb |= (__any_sync(kFullMask, imp[h]) ? 1u : 0u) << h;
+        uint32_t px = 0;
+        bool claim = false;
+  #pragma unroll
+        for (int h = 0; h < HS; ++h)
+          if (lane == (unsigned)h) {
+            px = ex[h];
+            claim = (anyb >> h) & 1u;
+          }
+        bool push = false;
+        uint32_t deg = 0;
+        if (claim) {
+          const uint4 d = a.qrow[px];
+          if (atomicExch(a.stamp + px, 1u) != 1u) {
+            push = true;
+            deg = d.w - d.x;
+          }
         }
-      bool push = false;
-      uint32_t deg = 0;
-      if (claim) {
-        const uint4 d = a.qrow[px];
-        if (atomicExch(a.stamp + px, 1u) != 1u) {
-          push = true;
-          deg = d.w - d.x;
-        }
+        stage_push_units(push, px, deg, a.cshift, st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
       }
-      stage_push_units(push, px, deg, a.cshift, st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
     }
   }
   stage_flush_cta(st, a.q1, &c->qn[1], a.qcap, c, a.qerr, lane);
@@ -161,12 +178,14 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
     for (uint32_t t0 = bt.first(); t0 < n; t0 = bt.next(lane)) {
       const uint32_t ui = t0 + grp;
       uint32_t beg = 0, end = 0, fe = 0, nfb = 0;
+      bool q1 = false;  // the unit's row belongs to the second query
       uint32_t sv[K];
 #pragma unroll
       for (int kk = 0; kk < K; ++kk) sv[kk] = Op::kIdentity;
       if (ui < n) {
         const unsigned long long u = qin[ui];  // written before the last barrier
         const uint32_t r = (uint32_t)u, ch = (uint32_t)(u >> 32);
+        q1 = r >= U0;
         const uint4 d = a.qrow[r];
         beg = d.x + (ch << a.cshift);
         end = min(d.w, beg + (1u << a.cshift));
@@ -234,7 +253,7 @@ __device__ bool relax_team(const RelaxArgs& a, const Team& t, unsigned long long
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) {
               if (want[h][kk]) {
-                const uint32_t cand = Op::relax(sv[kk], ewt[h]);
+                const uint32_t cand = relax_q<Op>(a, q1, sv[kk], ewt[h]);
                 if (Op::better(cand, curv[h][kk])) {
                   Op::red(row + kk * P, cand);
                   imp[h] = true;

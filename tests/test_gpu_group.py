@@ -114,6 +114,28 @@ def test_two_lane_groups_pull_every_round(svv, pair):
             np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L))
 
 
+@pytest.mark.parametrize("pair", [(0, 0), (1, 1), (2, 2), (3, 3), (0, 1), (1, 3), (2, 0), (1, 2)])
+def test_pair_tails_one_relaxation(svv, pair):
+    """A two-query group whose windows have one length runs both relaxations
+    as one launch over both queries' rows (a mixed pair in the min lattice,
+    SSWP rows complemented); one and two mask words, results equal the oracle
+    and the same pair with separate relaxations."""
+    log = W.scaled_rmat(scale=13, edge_factor=8, n_snapshots=100, rate=0.003, seed=53, add_mode="skewed")
+    hubs = _hubs(log, 4)
+    for L in (64, 100):
+        specs = [(pair[0], int(hubs[0]), 0, L), (pair[1], int(hubs[1 + (L & 1)]), 100 - L, L)]
+        with svv.Context(0) as ctx:
+            ctx.load_log(log)
+            ctx.set_tuning("group_mix", 1)
+            outs = _run(svv, ctx, specs, 2)
+            for (t, s, b, L2), o in zip(specs, outs):
+                np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L2))
+            ctx.set_tuning("pair_tails", 0)
+            sep = _run(svv, ctx, specs, 2)
+            for a, b in zip(outs, sep):
+                assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("pull", [1, 0])
 def test_group_hubs_equal_alone(svv, pull):
     """Deep solves from hub sources (pull rounds when the frontier is large,
