@@ -150,10 +150,10 @@ svv_status enqueue_group_bounds(svv_ctx* c, int t, const BatchInstance* inst, ui
 }
 
 // ---------------------------------------------------------------------------
-// Two-query tails.  The first query's stable compaction and subgraph go to
-// rows [0, U0) of the pair arrays, the second's after them (its extraction
-// reads the first query's counts on the device); one relaxation launch then
-// runs Algorithm 2 over both queries' rows with one frontier, and each query's
+// Two-query tails.  One extraction launch compacts both queries' unstable
+// vertices and builds both subgraphs into the pair arrays (the first query's
+// rows [0, U0), the second's after them); one relaxation launch then runs
+// Algorithm 2 over both queries' rows with one frontier, and each query's
 // scatter reads its own rows.  A pair of different types relaxes in the min
 // lattice (OpMixed), an SSWP query's rows on complemented widths.
 
@@ -165,7 +165,7 @@ void free_pair(svv_ctx* c) {
   c->p_qcw = nullptr;
   c->p_qmask = nullptr;
   c->p_val = nullptr;
-  c->p_q0 = c->p_q1 = nullptr;
+  c->p_q0 = c->p_q1 = c->p_units = nullptr;
   c->p_valcap = c->p_qcap = 0;
 }
 
@@ -182,6 +182,7 @@ svv_status ensure_pair_rows(svv_ctx* c, uint32_t LP) {
       (st = alloc_n(c, c->pair_bufs, 2 * (uint64_t)c->ecap, &c->p_qcw)) ||
       (st = alloc_n(c, c->pair_bufs, 2 * c->mcap, &c->p_qmask)) ||
       (st = alloc_n(c, c->pair_bufs, need_v, &c->p_val)) ||
+      (st = alloc_n(c, c->pair_bufs, 2 * (uint64_t)c->ucap, &c->p_units)) ||
       (st = alloc_n(c, c->pair_bufs, 2 * (uint64_t)c->qcap, &c->p_q0)) ||
       (st = alloc_n(c, c->pair_bufs, 2 * (uint64_t)c->qcap, &c->p_q1))) {
     free_pair(c);
@@ -210,36 +211,39 @@ svv_status enqueue_pair_tail(svv_ctx* c, const BatchInstance* inst, uint32_t* co
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl + 6, 0, sizeof(TeamCtl), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "memset");
   const uint32_t QW = ceil_div(wl, 64);
-  for (int qi = 0; qi < 2; ++qi) {
-    QrsArgs q{};
-    q.g = c->g;
-    q.win = Window{inst[qi].wb, wl};
-    q.QW = QW;
-    q.prune = c->prune ? 1 : 0;
-    q.rI = rI[qi];
-    q.rU = rU[qi];
-    q.row = qi ? c->p_row1 : c->row;
-    q.uv = c->p_uv;
-    q.part = c->part;
-    q.units = c->units;
-    q.ucap = c->ucap;
-    q.cshift = c->qrs_cs;
-    q.qcnt = c->p_qcnt;
-    q.qrow = c->p_qrow;
-    q.cur = c->p_cur;
-    q.qcw = c->p_qcw;
-    q.qmask = c->p_qmask;
-    q.ecap = (uint32_t)std::min<uint64_t>(2 * (uint64_t)c->ecap, 0xFFFFFFFFull);
-    q.mcap = 2 * c->mcap;
-    q.rowcap = 2 * c->g.V;
-    q.ctl = qi ? c->ctl + 6 : c->ctl + 2;
-    q.base = qi ? &(c->ctl + 2)->aux[0] : nullptr;
-    q.qerr = c->qerr;
-    q.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
-    LaunchCfg qc = cfg_for(c, c->occ_qrs, k0.bps);
-    if ((int64_t)qc.blocks > (int64_t)c->num_sms * 4) qc.blocks = c->num_sms * 4;
-    if ((e = launch_qrs(q, qc, s)) != cudaSuccess) return cuda_fail(c, e, "launch subgraph extraction");
-  }
+  // both queries' stable compaction and subgraph in one launch
+  QrsArgs q{};
+  q.g = c->g;
+  q.win = Window{inst[0].wb, wl};
+  q.win1 = Window{inst[1].wb, wl};
+  q.QW = QW;
+  q.prune = c->prune ? 1 : 0;
+  q.rI = rI[0];
+  q.rU = rU[0];
+  q.rI1 = rI[1];
+  q.rU1 = rU[1];
+  q.row = c->row;
+  q.row1 = c->p_row1;
+  q.counts1_out = &(c->ctl + 6)->aux[0];
+  q.uv = c->p_uv;
+  q.part = c->part;
+  q.units = c->p_units;
+  q.ucap = (uint32_t)std::min<uint64_t>(2 * (uint64_t)c->ucap, 0xFFFFFFFFull);
+  q.cshift = c->qrs_cs;
+  q.qcnt = c->p_qcnt;
+  q.qrow = c->p_qrow;
+  q.cur = c->p_cur;
+  q.qcw = c->p_qcw;
+  q.qmask = c->p_qmask;
+  q.ecap = (uint32_t)std::min<uint64_t>(2 * (uint64_t)c->ecap, 0xFFFFFFFFull);
+  q.mcap = 2 * c->mcap;
+  q.rowcap = 2 * c->g.V;
+  q.ctl = c->ctl + 2;
+  q.qerr = c->qerr;
+  q.spin_ns = (unsigned long long)c->spin_ms * 1000000ull;
+  LaunchCfg qc = cfg_for(c, c->occ_qrs, k0.bps);
+  if ((int64_t)qc.blocks > (int64_t)c->num_sms * 4) qc.blocks = c->num_sms * 4;
+  if ((e = launch_qrs(q, qc, s)) != cudaSuccess) return cuda_fail(c, e, "launch subgraph extraction");
   const bool mixed = inst[0].type != inst[1].type;
   auto kind_of = [](int t) { return t == 0 ? kKindSum : t == 1 ? kKindMaxNot : t == 2 ? kKindHop : kKindMax; };
   RelaxArgs r{};

@@ -133,11 +133,15 @@ struct QrsArgs {
   uint32_t* qerr;
   unsigned long long spin_ns;
   unsigned long long* trace;  // optional: start ns of each of the five passes, then the end
-  // null, or the counts (aux) of a query extracted before into the same
-  // arrays: this query's rows, edges and masks then follow that query's
-  // (two queries relaxed in one launch)
-  const unsigned int* base;
   uint32_t rowcap;        // rows the row arrays hold (uv, qrow; qcnt and cur hold 2 per row)
+  // a second query extracted in the same launch (rI1 null: none), same window
+  // length: its rows, units, edges and masks follow the first query's; its
+  // number of rows goes to counts1_out[0] (aux[0] holds the first query's)
+  const uint32_t* rI1;
+  const uint32_t* rU1;
+  uint32_t* row1;
+  Window win1;
+  unsigned int* counts1_out;
 };
 
 struct RelaxArgs {

@@ -71,8 +71,10 @@ __device__ __forceinline__ void block_sum4(uint32_t& a, uint32_t& b, uint32_t& c
 // Walk the edges of every unit in the queue (warp-balanced, as in the solve)
 // and classify each edge: all-window (F) or masked (M) kept edge.
 // FILL=false: add per-row counts; FILL=true: write the edges.
+// With a second query (a.rI1), rows from U0 on are that query's: its edges
+// are classified against its own row map and window.
 template <bool FILL>
-__device__ void qrs_walk(const QrsArgs& a, const Team& t, uint32_t NU, unsigned* ticket) {
+__device__ void qrs_walk(const QrsArgs& a, const Team& t, uint32_t NU, uint32_t U0, unsigned* ticket) {
   const DevGraph& g = a.g;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt = (1u << lane) - 1u;
@@ -123,7 +125,8 @@ __device__ void qrs_walk(const QrsArgs& a, const Team& t, uint32_t NU, unsigned*
         if (p < total) {
           const uint32_t e = bk + (p - (ik - ck));
           const uint2 ew = __ldg(g.cw + e);
-          rx[h] = a.row[ew.x];
+          const bool q1 = a.rI1 && rkk[h] >= U0;
+          rx[h] = (q1 ? a.row1 : a.row)[ew.x];
           w[h] = ew.y;
           if (rx[h] != kNone) {
             if (e < fk) {
@@ -131,7 +134,7 @@ __device__ void qrs_walk(const QrsArgs& a, const Team& t, uint32_t NU, unsigned*
             } else {
               m[h] = g.nfmask + (size_t)(nk + (e - fk)) * g.W;
               bool any, all;
-              window_any_all(m[h], a.win, any, all);
+              window_any_all(m[h], q1 ? a.win1 : a.win, any, all);
               isF[h] = all;
               isM[h] = any && !all;
             }
@@ -167,8 +170,9 @@ __device__ void qrs_walk(const QrsArgs& a, const Team& t, uint32_t NU, unsigned*
             a.qcw[pos] = make_uint2(rx[h], w[h]);
             const uint4 d = __ldcg(a.qrow + rk);
             uint64_t* out = a.qmask + (size_t)(d.z + (pos - d.y)) * a.QW;
+            const uint32_t wb = (a.rI1 && rk >= U0) ? a.win1.b : a.win.b;
             for (uint32_t j = 0; j < a.QW; ++j) {
-              uint64_t word = mask_extract(m[h], g.W, a.win.b + 64u * j);
+              uint64_t word = mask_extract(m[h], g.W, wb + 64u * j);
               const uint32_t left = a.win.l - 64u * j;
               if (left < 64u) word &= (1ull << left) - 1ull;
               out[j] = word;
@@ -187,43 +191,49 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
   if (cta_read(a.qerr) != 0u) return false;
   const uint32_t V = g.V;
   const uint32_t C = 1u << a.cshift;
-  // where this query's rows, edges and masks start (after a query extracted
-  // before into the same arrays)
-  uint32_t rbase = 0, ebase = 0, mbase = 0;
-  if (a.base) {
-    rbase = ld_cg(a.base + 0);
-    ebase = ld_cg(a.base + 2);
-    mbase = ld_cg(a.base + 3);
-  }
+  // A second query (a.rI1) is extracted in the same launch: its rows follow
+  // the first query's, its units follow theirs, and the row scan and the
+  // fill run over both ranges at once.
+  const int nq = a.rI1 ? 2 : 1;
 
-  // ---- P1: unstable vertices and their units, per CTA vertex range
+  // ---- P1: unstable vertices and their units, per CTA vertex range and query
   if (a.trace && b == 0 && tid == 0) a.trace[0] = global_ns();
   const unsigned long long per = (((unsigned long long)V + nb - 1) / nb + 31ull) & ~31ull;
   const uint32_t lo = (uint32_t)min((unsigned long long)V, per * b);
   const uint32_t hi = (uint32_t)min((unsigned long long)V, per * b + per);
   {
-    uint32_t cnt = 0, nun = 0, z0 = 0, z1 = 0;
+    uint32_t cnt = 0, nun = 0, cnt1 = 0, nun1 = 0;
     for (uint32_t v = lo + tid; v < hi; v += blockDim.x) {
+      const uint32_t nv = (__ldg(g.rp + v + 1) - __ldg(g.rp + v) + C - 1u) >> a.cshift;
       if (!a.prune || a.rI[v] != a.rU[v]) {
         ++cnt;
-        nun += (__ldg(g.rp + v + 1) - __ldg(g.rp + v) + C - 1u) >> a.cshift;
+        nun += nv;
+      }
+      if (nq > 1 && (!a.prune || a.rI1[v] != a.rU1[v])) {
+        ++cnt1;
+        nun1 += nv;
       }
     }
-    block_sum4(cnt, nun, z0, z1);
+    block_sum4(cnt, nun, cnt1, nun1);
     if (tid == 0) {
-      a.part[2 * b] = cnt;
-      a.part[2 * b + 1] = nun;
+      a.part[4 * b] = cnt;
+      a.part[4 * b + 1] = nun;
+      a.part[4 * b + 2] = cnt1;
+      a.part[4 * b + 3] = nun1;
     }
   }
   if (!t.sync()) return false;
 
-  // ---- P2: rows and units in vertex order
+  // ---- P2: rows and units in vertex order, the first query's then the second's
   if (a.trace && b == 0 && tid == 0) a.trace[1] = global_ns();
-  uint32_t U = 0, NU = 0;
-  {
+  uint32_t U = 0, NU = 0, U0 = 0;
+  for (int qi = 0; qi < nq; ++qi) {
+    const uint32_t* qI = qi ? a.rI1 : a.rI;
+    const uint32_t* qU = qi ? a.rU1 : a.rU;
+    uint32_t* qrowmap = qi ? a.row1 : a.row;
     uint32_t o_r = 0, o_u = 0, t_r = 0, t_u = 0;
     for (uint32_t j = tid; j < nb; j += blockDim.x) {
-      const uint32_t pr = ld_cg(a.part + 2 * j), pu = ld_cg(a.part + 2 * j + 1);
+      const uint32_t pr = ld_cg(a.part + 4 * j + 2 * qi), pu = ld_cg(a.part + 4 * j + 2 * qi + 1);
       t_r += pr;
       t_u += pu;
       if (j < b) {
@@ -232,20 +242,26 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
       }
     }
     block_sum4(o_r, o_u, t_r, t_u);
-    U = t_r;
-    NU = t_u;
+    const uint32_t rbase = U, ubase = NU;  // after the first query's rows and units
+    U += t_r;
+    NU += t_u;
+    if (qi == 0) U0 = t_r;
     if (b == 0 && tid == 0) {
-      c->aux[0] = U;
-      c->aux[1] = NU;
+      if (qi == 0) {
+        c->aux[0] = t_r;
+        c->aux[1] = t_u;
+      } else {
+        a.counts1_out[0] = t_r;
+      }
     }
-    if (NU > a.ucap || (unsigned long long)rbase + U > a.rowcap) {
+    if (NU > a.ucap || U > a.rowcap) {
       if (tid == 0) set_err(c, a.qerr, kErrInternal);
       return false;  // every CTA sees the same totals and leaves here
     }
     for (uint32_t base = lo; base < hi; base += blockDim.x) {
       const uint32_t v = base + tid;
       uint32_t flag = 0, nu = 0;
-      if (v < hi && (!a.prune || a.rI[v] != a.rU[v])) {
+      if (v < hi && (!a.prune || qI[v] != qU[v])) {
         flag = 1;
         nu = (__ldg(g.rp + v + 1) - __ldg(g.rp + v) + C - 1u) >> a.cshift;
       }
@@ -253,7 +269,7 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
       block_excl_scan2(flag, nu, ef, eu, tf, tu);
       const uint32_t r = rbase + o_r + ef;
       if (v < hi) {
-        a.row[v] = flag ? r : kNone;
+        qrowmap[v] = flag ? r : kNone;
         if (flag) {
           a.uv[r] = v;
           a.qcnt[2 * r] = 0u;
@@ -271,7 +287,7 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
         const uint32_t ik = __shfl_sync(kFullMask, incl, k), nk = __shfl_sync(kFullMask, nu, k);
         const uint32_t rk = __shfl_sync(kFullMask, r, k), ek = __shfl_sync(kFullMask, eu, k);
         const uint32_t jj = j - (ik - nk);
-        if (j < wtot) a.units[o_u + ek + jj] = (unsigned long long)rk | ((unsigned long long)jj << 32);
+        if (j < wtot) a.units[ubase + o_u + ek + jj] = (unsigned long long)rk | ((unsigned long long)jj << 32);
       }
       o_r += tf;
       o_u += tu;
@@ -281,14 +297,14 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
 
   // ---- P3: per-row counts of kept edges
   if (a.trace && b == 0 && tid == 0) a.trace[2] = global_ns();
-  qrs_walk<false>(a, t, NU, &c->ticket[0]);
+  qrs_walk<false>(a, t, NU, U0, &c->ticket[0]);
   if (!t.sync()) return false;
 
   // ---- P4: scan rows
   if (a.trace && b == 0 && tid == 0) a.trace[3] = global_ns();
   const unsigned long long rper = (((unsigned long long)U + nb - 1) / nb + 31ull) & ~31ull;
-  const uint32_t rlo = rbase + (uint32_t)min((unsigned long long)U, rper * b);
-  const uint32_t rhi = rbase + (uint32_t)min((unsigned long long)U, rper * b + rper);
+  const uint32_t rlo = (uint32_t)min((unsigned long long)U, rper * b);
+  const uint32_t rhi = (uint32_t)min((unsigned long long)U, rper * b + rper);
   {
     uint32_t se = 0, sm = 0, z0 = 0, z1 = 0;
     for (uint32_t r = rlo + tid; r < rhi; r += blockDim.x) {
@@ -319,7 +335,7 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
       c->aux[2] = t_e;
       c->aux[3] = t_m;
     }
-    if ((unsigned long long)ebase + t_e > a.ecap || ((unsigned long long)mbase + t_m) * a.QW > a.mcap) {
+    if (t_e > a.ecap || (unsigned long long)t_m * a.QW > a.mcap) {
       if (tid == 0) set_err(c, a.qerr, kErrInternal);
       return false;
     }
@@ -333,8 +349,8 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
       uint32_t ee, em, te, tm;
       block_excl_scan2(f + m, m, ee, em, te, tm);
       if (r < rhi) {
-        const uint32_t start = ebase + o_e + ee;
-        a.qrow[r] = make_uint4(start, start + f, mbase + o_m + em, start + f + m);
+        const uint32_t start = o_e + ee;
+        a.qrow[r] = make_uint4(start, start + f, o_m + em, start + f + m);
         a.cur[2 * r] = start;
         a.cur[2 * r + 1] = start + f;
       }
@@ -346,7 +362,7 @@ __device__ inline bool qrs_team(const QrsArgs& a, const Team& t) {
 
   // ---- P5: fill
   if (a.trace && b == 0 && tid == 0) a.trace[4] = global_ns();
-  qrs_walk<true>(a, t, NU, &c->ticket[1]);
+  qrs_walk<true>(a, t, NU, U0, &c->ticket[1]);
   if (a.trace && tid == 0) atomicMax(a.trace + 5, global_ns());  // the last CTA to finish
   return true;
 }
