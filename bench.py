@@ -991,10 +991,11 @@ def main():
         dom = max(phases, key=lambda p: p["avg_launch_ms"])
         if groups and len(grouped) > 1:
             ph_step = {k: (group_ms[k] / nphase if k in group_ms else v / nphase) for k, v in phase_ms.items()}
-            # lane words, two group solves, split; per member extraction and
-            # scatter, and one relaxation for a pair of one window length
+            # lane words, two group solves, split; per member extraction,
+            # relaxation and scatter, or for a pair of one window length one
+            # extraction, one relaxation and two scatters
             pair = len(grouped) == 2 and grouped[0].win_len == grouped[1].win_len and grouped[0].win_len <= 128
-            launches = len(qs) - len(grouped) + 4 + (5 if pair else 3 * len(grouped))
+            launches = len(qs) - len(grouped) + 4 + (4 if pair else 3 * len(grouped))
             api = ("svv_query_batch: the step's queries in one call, one query group of mixed types "
                    "(batch_mode 2, group_mix 1); the call returns after the step")
         else:
