@@ -92,6 +92,27 @@ def test_floyd_warshall(kind, qtype, seed):
         np.testing.assert_array_equal(got.astype(np.uint64), fw[s])
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_widest_path_is_complemented_narrowest_path(seed):
+    """The identity query groups of mixed types rely on: the widest-path width
+    (max over paths of the min weight; 0 = unreachable, the source infinite)
+    is the complement of the min over paths of the max COMPLEMENTED weight,
+    i.e. SSWP(w) = ~SSNP(~w), with 0 and 2^32-1 among the weights."""
+    rng = np.random.default_rng(300 + seed)
+    V = int(rng.integers(5, 65))
+    m = int(rng.integers(V, 4 * V))
+    src, dst, _ = _random_graph(rng, V, m)
+    w = rng.integers(0, 1 << 32, m, dtype=np.uint64).astype(np.uint32)
+    w[: m // 8] = rng.choice(np.array([0, 1, 0xFFFFFFFE, 0xFFFFFFFF], np.uint32), m // 8)
+    rp, col, ww = _csr(V, src, dst, w)
+    for s in sorted({0, V - 1, int(rng.integers(0, V))}):
+        wide = oracle.solve(oracle.SSWP, V, rp, col, ww, s)
+        narrow_c = oracle.solve(oracle.SSNP, V, rp, col, ~ww, s)
+        np.testing.assert_array_equal(wide, ~narrow_c)
+        # and both against Floyd-Warshall over their own semirings
+        np.testing.assert_array_equal(wide.astype(np.uint64), _fw(V, src, dst, w, "sswp")[s])
+
+
 def _scipy_matrix(V, rp, col, w, unit=False):
     rows = np.repeat(np.arange(V), np.diff(rp.astype(np.int64)))
     ww = np.ones_like(w, dtype=np.float64) if unit else w.astype(np.float64)
