@@ -157,7 +157,7 @@ def graph_counts(log, rp, mask):
     return {"V": log.V, "E": int(m.shape[0]), "NF": int((~full).sum()), "W": Wd}
 
 
-def survey_bytes(phase, gc, st, L):
+def algorithmic_bytes(phase, gc, st, L):
     """Algorithmic bytes of one launch of a phase by the per-unit figures of
     the hot-path table (instances of 8 + 8W bytes, values and row offsets):
     each bound solve makes one pass over the union graph, the compaction reads
@@ -917,7 +917,7 @@ def main():
             pms += ps.elapsed_time(pe)
         pms = max_over_ranks(pms, world, f"cuda:{dev}")
         pvalue = values_per_step * args.plain_steps * world / (pms / 1e3)
-        pbytes = sum(survey_bytes("plain", gc, None, q.win_len) for q in qs)
+        pbytes = sum(algorithmic_bytes("plain", gc, None, q.win_len) for q in qs)
         plain = {"value": pvalue, "unit": UNIT, "ms_per_step": pms / args.plain_steps,
                  "iu_speedup": value / pvalue, "algorithmic_gbs": pbytes / (pms / args.plain_steps / 1e3) / 1e9}
 
@@ -975,12 +975,12 @@ def main():
                 # algorithmic bytes are the member queries' (one unit each),
                 # its floor reads the graph once for all of them
                 ms = group_ms[ph] / nphase
-                sb = sum(survey_bytes(ph, gc, None, q.win_len) for q in grouped)
+                sb = sum(algorithmic_bytes(ph, gc, None, q.win_len) for q in grouped)
                 lb = group_layout_bytes(ph, gc, len(grouped))
                 kname, tkey = GROUP_KERNELS[ph], "group_" + ph
             else:
                 ms = phase_ms[ph] / nlaunch
-                sb = sum(survey_bytes(ph, gc, st, q.win_len) for sts in all_stats for st, q in zip(sts, qs)) / nlaunch
+                sb = sum(algorithmic_bytes(ph, gc, st, q.win_len) for sts in all_stats for st, q in zip(sts, qs)) / nlaunch
                 lb = sum(layout_bytes(ph, gc, st, q.win_len) for sts in all_stats for st, q in zip(sts, qs)) / nlaunch
                 kname, tkey = PHASE_KERNELS[ph], ph
             a = sb / (ms / 1e3) / 1e9 if ms > 0 else 0.0
