@@ -626,6 +626,7 @@ svv_status enqueue_isolated(svv_ctx* c, int t, uint32_t source, uint32_t wl, uin
   if (e != cudaSuccess) return cuda_fail(c, e, "launch isolated-source fill");
   c->last_rI = c->rI;
   c->last_rU = c->rU;
+  c->last_row = c->row;
   if (co) {
     const size_t n = (size_t)c->g.V * sizeof(uint32_t);
     if (co->cap_out && (e = cudaMemcpyAsync(co->cap_out, c->rI, n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
@@ -695,6 +696,7 @@ svv_status enqueue_tail(svv_ctx* c, int t, uint32_t wb, uint32_t wl, uint32_t* o
     return cuda_fail(c, e, "memset");
   c->last_rI = rI;
   c->last_rU = rU;
+  c->last_row = c->row;
   // a3+a4: stable compaction and the Q-relevant subgraph
   QrsArgs q{};
   q.g = c->g;
@@ -1256,7 +1258,8 @@ svv_status svv_get_bounds(svv_ctx* c, uint32_t* cap, uint32_t* cup, uint32_t* ro
   const uint32_t* rU = c->last_rU ? c->last_rU : c->rU;
   if (cap) e = cudaMemcpyAsync(cap, rI, n, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess && cup) e = cudaMemcpyAsync(cup, rU, n, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && row) e = cudaMemcpyAsync(row, c->row, n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && row)
+    e = cudaMemcpyAsync(row, c->last_row ? c->last_row : c->row, n, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "copying bounds");
   return SVV_OK;

@@ -253,6 +253,7 @@ struct svv_ctx {
   // bounds the last query's phases read (svv_get_bounds)
   const uint32_t* last_rI = nullptr;
   const uint32_t* last_rU = nullptr;
+  const uint32_t* last_row = nullptr;  // its vertex -> relaxation-row map (a pair's second query: the pair arrays')
 
   svv_stats stats{};
 };

@@ -9,7 +9,7 @@
 namespace svv {
 
 void free_group(svv_ctx* c) {
-  c->last_rI = c->last_rU = nullptr;
+  c->last_rI = c->last_rU = c->last_row = nullptr;
   for (void* p : c->group_bufs) cudaFree(p);
   c->group_bufs.clear();
   c->gcap = c->gcup = c->gnfl = c->gipl = c->gerr = nullptr;
@@ -158,6 +158,7 @@ svv_status enqueue_group_bounds(svv_ctx* c, int t, const BatchInstance* inst, ui
 // lattice (OpMixed), an SSWP query's rows on complemented widths.
 
 void free_pair(svv_ctx* c) {
+  if (c->p_row1 && c->last_row == c->p_row1) c->last_row = nullptr;
   for (void* p : c->pair_bufs) cudaFree(p);
   c->pair_bufs.clear();
   c->p_uv = c->p_qcnt = c->p_cur = c->p_stamp = c->p_row1 = nullptr;
@@ -210,6 +211,9 @@ svv_status enqueue_pair_tail(svv_ctx* c, const BatchInstance* inst, uint32_t* co
   cudaError_t e = cudaMemsetAsync(c->ctl + 2, 0, sizeof(TeamCtl) * 2, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl + 6, 0, sizeof(TeamCtl), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+  c->last_rI = rI[1];  // svv_get_bounds: the batch's last instance
+  c->last_rU = rU[1];
+  c->last_row = c->p_row1;
   const uint32_t QW = ceil_div(wl, 64);
   // both queries' stable compaction and subgraph in one launch
   QrsArgs q{};

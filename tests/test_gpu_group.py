@@ -130,6 +130,14 @@ def test_pair_tails_one_relaxation(svv, pair):
             outs = _run(svv, ctx, specs, 2)
             for (t, s, b, L2), o in zip(specs, outs):
                 np.testing.assert_array_equal(svv.to_u32(o), oracle.query(log, t, s, b, L2))
+            # the bounds and row map of the batch's last query
+            cap, cup, row = (torch.empty(log.V, dtype=torch.int32, device="cuda") for _ in range(3))
+            svv.svv_get_bounds(ctx.h, cap, cup, row)
+            t, s, b, L2 = specs[1]
+            want_cap, want_cup = oracle.bounds(log, t, s, b, L2)
+            np.testing.assert_array_equal(svv.to_u32(cap), want_cap)
+            np.testing.assert_array_equal(svv.to_u32(cup), want_cup)
+            assert np.array_equal(svv.to_u32(row) == 0xFFFFFFFF, want_cap == want_cup)
             ctx.set_tuning("pair_tails", 0)
             sep = _run(svv, ctx, specs, 2)
             for a, b in zip(outs, sep):
