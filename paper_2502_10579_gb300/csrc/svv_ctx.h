@@ -190,7 +190,7 @@ struct svv_ctx {
   uint64_t* p_qmask = nullptr;
   uint32_t* p_val = nullptr;
   unsigned long long *p_q0 = nullptr, *p_q1 = nullptr, *p_units = nullptr;
-  uint64_t p_valcap = 0, p_qcap = 0;
+  uint64_t p_valcap = 0, p_qcap = 0, p_mcap = 0;
   bool pair_tails = true;  // run a two-query group's relaxations in one launch
   // svv_query_batch with host outputs: two staging slots and a copy stream
   uint32_t* bstage[2] = {nullptr, nullptr};

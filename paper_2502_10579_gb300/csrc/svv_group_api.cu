@@ -167,13 +167,14 @@ void free_pair(svv_ctx* c) {
   c->p_qmask = nullptr;
   c->p_val = nullptr;
   c->p_q0 = c->p_q1 = c->p_units = nullptr;
-  c->p_valcap = c->p_qcap = 0;
+  c->p_valcap = c->p_qcap = c->p_mcap = 0;
 }
 
 svv_status ensure_pair_rows(svv_ctx* c, uint32_t LP) {
   const uint64_t V = c->g.V;
   const uint64_t need_v = 2 * V * LP;
-  if (c->p_uv && need_v <= c->p_valcap) return SVV_OK;
+  // the mask capacity follows the longest window seen (ensure_window)
+  if (c->p_uv && need_v <= c->p_valcap && 2 * c->mcap <= c->p_mcap) return SVV_OK;
   free_pair(c);
   // every array holds two queries' worth of what the single-query scratch holds
   svv_status st;
@@ -190,6 +191,7 @@ svv_status ensure_pair_rows(svv_ctx* c, uint32_t LP) {
     return st;
   }
   c->p_valcap = need_v;
+  c->p_mcap = 2 * c->mcap;
   c->p_qcap = 2 * (uint64_t)c->qcap;
   return SVV_OK;
 }
@@ -240,7 +242,7 @@ svv_status enqueue_pair_tail(svv_ctx* c, const BatchInstance* inst, uint32_t* co
   q.qcw = c->p_qcw;
   q.qmask = c->p_qmask;
   q.ecap = (uint32_t)std::min<uint64_t>(2 * (uint64_t)c->ecap, 0xFFFFFFFFull);
-  q.mcap = 2 * c->mcap;
+  q.mcap = c->p_mcap;  // what the pair mask array holds
   q.rowcap = 2 * c->g.V;
   q.ctl = c->ctl + 2;
   q.qerr = c->qerr;
